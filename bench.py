@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark of the fused GI-preconditioned cascaded stream-collide step.
+
+Workload (default): 4096 x 4096 lid-driven cavity, U = 0.1, Re = 1000,
+gamma = 0.5, FP32 storage and collision, started from rest.  A "step" is one
+full time step of the domain (one launch of the stream-collide kernel).
+
+Prints one JSON line (rank 0).  value = cell updates per second over all
+ranks (MLUPS); each rank advances its own replica of the domain (the path is
+data-parallel over independent domains; no collective on the data path), so
+scaling is weak.  Inputs (1.2 GB of populations per replica) exceed the 129 MB
+L2, so no L2 flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and steady-state solves/sec (FP16-storage batched vs plain FP32) at L2≤1e-3"
+BYTES_PER_CELL = {"f32": 72, "f16": 36, "bf16": 36, "f64": 144}
+STORAGE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3}
+KERNEL_SOURCES = ["paper_1806_10251_gb300/csrc/stream_collide.cuh",
+                  "paper_1806_10251_gb300/csrc/d2q9_collide.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=list(STORAGE_CODE), default="f32")
+    ap.add_argument("--n", type=int, default=4096, help="cavity side")
+    ap.add_argument("--gamma", type=float, default=0.5)
+    ap.add_argument("--Re", type=float, default=1000.0)
+    ap.add_argument("--gi-mode", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-check-every", type=int, default=100)
+    return ap.parse_args()
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fp:
+            h.update(fp.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fp:
+            d = json.load(fp)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(storage: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", f"stream_collide_{storage}_cavity{n}.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_sources_sha256") != kernel_hash():
+        return None
+    try:
+        return int(float(vals["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.proc = None
+        self.device_id = device_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.device_id:
+            cmd += ["-i", self.device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(case_fn, seconds_target=15.0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded sample."""
+    import oracle as orc
+    c = case_fn()
+    d = orc.Domain(c.nx, c.ny, c.nu, c.gamma, c.sides)
+    d.init_equilibrium()
+    d.step(1)  # first touch
+    t = time.perf_counter()
+    d.step(1)
+    one = time.perf_counter() - t
+    n = max(1, min(50, int(seconds_target / max(one, 1e-6))))
+    t = time.perf_counter()
+    d.step(n)
+    el = time.perf_counter() - t
+    return {"value": c.cells * n / el / 1e6, "unit": "MLUPS", "cores": orc.get_threads(), "kind": "oracle",
+            "sample": f"{c.name}: {n} oracle steps of the full domain (FP64, OpenMP over rows)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle as orc
+    import workloads as wl
+    # bounded sample of the workload: a 1024 x 1024 cavity at the same Re/U/gamma
+    # (per-cell work is identical; the full 4096^2 domain needs ~1 s per oracle step)
+    side = min(args.n, 1024)
+    c = wl.cavity(side, args.Re, 0.1, args.gamma)
+    d = orc.Domain(c.nx, c.ny, c.nu, c.gamma, c.sides, gi_mode=args.gi_mode)
+    d.init_equilibrium()
+    d.step(args.warmup)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        d.step(1)
+    el = time.perf_counter() - t
+    v = c.cells * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"cavity {side}x{side} sample of the {args.n}x{args.n} cavity, U=0.1, "
+                                   f"Re={args.Re:g}, gamma={args.gamma:g}, from rest", "storage": "f64"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": orc.get_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps of a {side}x{side} cavity"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1806_10251_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    lbm.use_torch_allocator()
+    case = wl.cavity(args.n, args.Re, 0.1, args.gamma)
+    g = lbm.Solver(case.nx, case.ny, case.nu, case.gamma, case.U)
+    g.set_option("gi_mode", args.gi_mode)
+    if args.storage != "f32":
+        g.set_option("storage", STORAGE_CODE[args.storage])
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream.cuda_stream)
+
+    # ---- device-resident throughput (value) --------------------------------
+    for _ in range(args.warmup):
+        g.step(1)
+    torch.cuda.synchronize()
+    barrier()
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        dev_id = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        dev_id = None
+    clocks = ClockSampler(dev_id)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = g.kernel_launches
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = g.kernel_launches - l0
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = case.cells
+    value = cells * args.steps * world / (ms / 1e3) / 1e6
+    per_launch_s = ms / 1e3 / args.steps
+    bpc = BYTES_PER_CELL[args.storage]
+    achieved = bpc * cells / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    r, _ = g.residual()
+    assert np.isfinite(r), "non-finite state after the timed steps"
+
+    # ---- end to end through the public API with pinned host buffers --------
+    ce = max(1, min(args.e2e_check_every, args.steps))
+    nchunks = max(1, args.steps // ce)
+    e2e_steps = nchunks * ce
+    pin = lambda: torch.empty((case.ny, case.nx), dtype=torch.float64, pin_memory=True).numpy()
+    rho0, ux0, uy0 = pin(), pin(), pin()
+    rho0[:] = 1.0
+    ux0[:] = 0.0
+    uy0[:] = 0.0
+    outs = (pin(), pin(), pin())
+    g2 = lbm.Solver(case.nx, case.ny, case.nu, case.gamma, case.U)
+    g2.set_option("gi_mode", args.gi_mode)
+    if args.storage != "f32":
+        g2.set_option("storage", STORAGE_CODE[args.storage])
+    g2.set_stream(stream.cuda_stream)
+    g2.init_fields(rho0, ux0, uy0)
+    g2.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    g2.init_fields(rho0, ux0, uy0)
+    for _ in range(nchunks):
+        g2.step(ce)
+        g2.residual()
+    g2.fields(out=outs)
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    field_bytes = 3 * cells * 8
+    e2e = {"value": cells * e2e_steps * world / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": field_bytes / e2e_steps,
+           "d2h_bytes_per_step": (field_bytes + nchunks * 40) / e2e_steps,
+           "calls": f"lbm_init_fields + {nchunks} x (lbm_step({ce}) + lbm_residual) + lbm_fields, pinned host arrays"}
+    g2.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage != "f64" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"lid-driven cavity {args.n}x{args.n}, U=0.1, Re={args.Re:g}, "
+                                   f"gamma={args.gamma:g}, GI mode {args.gi_mode}, from rest",
+                       "storage": args.storage, "replicas": world,
+                       "l2": "no flush: populations (per replica) exceed the 129 MB L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": profiled_traffic(args.storage, args.n),
+                         "bytes_per_cell": bpc, "kernel": "stream_collide_kernel"},
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(lambda: wl.cavity(args.n, args.Re, 0.1, args.gamma))
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the Galilean-invariant
+ * preconditioned cascaded central-moment lattice Boltzmann method on the D2Q9
+ * lattice (Hajabdollahi & Premnath, arXiv 1806.10251).
+ *
+ * What one step computes (pull form of Eq. 2): every fluid cell pulls its nine
+ * post-collision populations from the upwind neighbours (Eq. 2b; half-way
+ * bounce-back with the moving-wall momentum term at walls and solid cells),
+ * forms raw moments (Eq. 3), the density gradient by central differences, the
+ * diagonal strain rates from the second-order non-equilibrium moments
+ * (Eqs. 51-55), the extended-equilibrium corrections (Eqs. 33, 45-47), and
+ * relaxes through the cascaded kernel of Sec. 5 (Eq. 4 when uncorrected), then
+ * stores f~ = fbar + K g + S (Eq. 2a).
+ *
+ * Conventions
+ *  - Every call returns an lbm_status; nothing throws across the ABI.
+ *    lbm_last_error() gives a thread-local message for the last failure.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Outputs go
+ *    to caller-owned host arrays.  Field arrays are nx*ny doubles, index
+ *    y*nx + x (x fastest).  Population arrays are 9*nx*ny doubles, index
+ *    alpha*nx*ny + y*nx + x, with the velocity ordering
+ *      0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *  - A context owns its device memory and is not thread-safe; different
+ *    contexts may be used from different threads.
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    needs one returns LBM_ERR_CUDA.
+ *  - Observation point: after lbm_step(n) the stored state is the
+ *    post-collision array of step n.  lbm_fields returns the density and
+ *    velocity that step n's collision used: rho = sum f~, rho u = sum f~ e -
+ *    F/(2 gamma) (the collision conserves rho and adds exactly F/gamma to rho u).
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID = -1,        /* bad argument (message says which)          */
+    LBM_ERR_OOM = -2,            /* device or host allocation failed            */
+    LBM_ERR_CUDA = -3,           /* CUDA runtime error or no device             */
+    LBM_ERR_DIVERGED = -4,       /* NaN/Inf in the fields                       */
+    LBM_ERR_NOT_CONVERGED = -5,  /* max_steps reached above the tolerance       */
+    LBM_ERR_TIMEOUT = -6,        /* wall-clock limit reached                    */
+    LBM_ERR_IO = -7              /* checkpoint file could not be read/written   */
+} lbm_status;
+
+typedef enum { LBM_SIDE_PERIODIC = 0, LBM_SIDE_WALL = 1, LBM_SIDE_MOVING_WALL = 2 } lbm_side_kind;
+
+typedef struct {
+    int kind;          /* lbm_side_kind                                     */
+    double ux, uy;     /* wall velocity (LBM_SIDE_MOVING_WALL only)         */
+} lbm_side;
+
+/* Opposite sides must both be periodic or both non-periodic.  A link whose
+ * source lies beyond one side takes that side's wall velocity; a link whose
+ * source lies beyond two sides (a corner) sees a stationary wall.  The solid
+ * mask (optional, nx*ny bytes, non-zero = solid, copied) adds stationary
+ * bounce-back obstacles. */
+typedef struct {
+    lbm_side west, east, south, north;
+    const uint8_t *solid;
+} lbm_boundaries;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Storage formats of the population arrays (collision is FP32 for the first
+ * three, FP64 for the last).  Populations are stored as deviations
+ * f_alpha - w_alpha rho0 from the rest state (rho0 = 1). */
+enum { LBM_STORAGE_F32 = 0, LBM_STORAGE_F16 = 1, LBM_STORAGE_BF16 = 2, LBM_STORAGE_F64 = 3 };
+/* Collision kernels: Eq. 4 (uncorrected), Eq. 4 with the gamma^2-scaled cubic
+ * third-order equilibria only, and the full Sec. 5 kernel (default). */
+enum { LBM_GI_UNCORRECTED = 0, LBM_GI_CUBIC_ONLY = 1, LBM_GI_FULL = 2 };
+
+/* Create a domain of nx x ny cells (nx, ny >= 3) with kinematic viscosity nu
+ * (> 0; omega4 = omega5 = 1/(3 nu/gamma + 1/2), Eq. 49), preconditioning
+ * parameter gamma in (0, 1], and reference speed U (>= 0).  bnd == NULL gives
+ * the lid-driven cavity: stationary west/east/south walls, north wall moving
+ * at (U, 0).  The state starts at rest (rho = 1, u = 0).  *out receives the
+ * context on success and NULL on failure. */
+lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U,
+                      const lbm_boundaries *bnd, lbm_ctx **out);
+
+/* Options (before or between steps):
+ *   "omega3", "omega6", "omega7", "omega8"  relaxation rates in (0, 2), default 1
+ *   "gi_mode"   LBM_GI_* (default LBM_GI_FULL)
+ *   "storage"   LBM_STORAGE_* (default F32); changing it re-encodes the state
+ *   "fx", "fy"  uniform body force (default 0)
+ *   "guard"     1 = drop the velocity-dependent parts of the strain-rate solve
+ *               where |D| < 0.1 |D0| (Eqs. 53-55; off by default), counted
+ *   "cells_per_item" rows per work item of the step kernel (tuning; >= 1) */
+lbm_status lbm_set_option(lbm_ctx *ctx, const char *key, double value);
+lbm_status lbm_get_option(lbm_ctx *ctx, const char *key, double *value);
+
+/* Launch on this CUDA stream (a cudaStream_t; NULL = the context's own). */
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *stream);
+
+/* Per-cell body force (host arrays nx*ny, copied); NULL, NULL removes it. */
+lbm_status lbm_set_force_field(lbm_ctx *ctx, const double *fx, const double *fy);
+
+/* Initialise the state to f~0 = f_eq(rho, u) - S/2 with the Eq. 15 raw
+ * equilibria (fourth moment such that the central fourth moment is rho/9).
+ * NULL fields mean rho = 1 / u = 0.  Resets the step counter. */
+lbm_status lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *ux, const double *uy);
+
+/* Advance n >= 0 steps.  Asynchronous with respect to the host. */
+lbm_status lbm_step(lbm_ctx *ctx, long n);
+
+/* March to steady state: every check_every steps compute
+ * r = ||u^n - u^(n - check_every)||_2 / ||u^n||_2 over fluid cells in FP64 and
+ * stop when r < tol.  NaN/Inf gives LBM_ERR_DIVERGED; reaching max_steps gives
+ * LBM_ERR_NOT_CONVERGED; wall_seconds > 0 bounds the wall time (LBM_ERR_TIMEOUT).
+ * steps_done / final_residual may be NULL. */
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, long check_every, long max_steps,
+                             double wall_seconds, long *steps_done, double *final_residual);
+
+/* One convergence check now: residual against the previous check (or the
+ * initial state), then the snapshot is replaced.  sums (may be NULL) receives
+ * {sum |du|^2, sum |u|^2, sum rho, sum rho ux, sum rho uy} over fluid cells. */
+lbm_status lbm_residual(lbm_ctx *ctx, double *residual, double sums[5]);
+
+/* Density and velocity (see the observation point above); NULL skips a field;
+ * solid cells give NaN.  Synchronises the context's stream. */
+lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *ux, double *uy);
+
+/* Full populations f (not deviations), 9*nx*ny doubles, for checks and restart. */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f);
+
+lbm_status lbm_steps_done(lbm_ctx *ctx, long *steps);
+lbm_status lbm_guard_count(lbm_ctx *ctx, long *count);
+
+/* Checkpoint: the stored post-collision array (in its storage format), step
+ * count and parameters.  lbm_load needs a context of the same size. */
+lbm_status lbm_save(lbm_ctx *ctx, const char *path);
+lbm_status lbm_load(lbm_ctx *ctx, const char *path);
+
+void lbm_destroy(lbm_ctx *ctx);           /* NULL-safe */
+const char *lbm_last_error(void);         /* thread-local, never NULL */
+
+/* Device memory provider (process-wide).  alloc returns a device pointer of at
+ * least `bytes` bytes aligned to 256 bytes, or NULL; release frees it.  NULL
+ * restores cudaMalloc/cudaFree.  Set it before creating contexts. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*release)(void *ptr, void *user);
+    void *user;
+} lbm_allocator;
+lbm_status lbm_set_allocator(const lbm_allocator *a);
+
+/* Number of step-kernel launches made by this context so far. */
+lbm_status lbm_kernel_launches(lbm_ctx *ctx, long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

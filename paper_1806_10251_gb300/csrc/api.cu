@@ -1,0 +1,702 @@
+// C ABI of the library: context lifetime, options, stepping, convergence,
+// field and population I/O, checkpoints.  Every entry point returns a status;
+// the message of the last failure is kept per thread.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+int blocks_per_sm_f32(int gi_mode);
+int blocks_per_sm_f16(int gi_mode);
+int blocks_per_sm_bf16(int gi_mode);
+int blocks_per_sm_f64(int gi_mode);
+}  // namespace lbm
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_error = "no error";
+
+lbm_status fail(lbm_status s, const std::string &msg)
+{
+    g_error = msg;
+    return s;
+}
+
+lbm_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call)                                            \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+lbm_allocator g_alloc = {nullptr, nullptr, nullptr};
+
+void *dev_alloc(size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (g_alloc.alloc) return g_alloc.alloc(bytes, g_alloc.user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void *p)
+{
+    if (!p) return;
+    if (g_alloc.release) g_alloc.release(p, g_alloc.user);
+    else cudaFree(p);
+}
+
+// RAII holder for temporary device buffers.
+struct DevBuf {
+    void *p = nullptr;
+    explicit DevBuf(size_t bytes) : p(dev_alloc(bytes)) {}
+    ~DevBuf() { dev_free(p); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, pitch = 0;
+    long long plane = 0;
+    double nu = 0, gamma = 1, U = 0;
+    double omega[9] = {0, 0, 0, 1, 1, 1, 1, 1, 1};
+    int gi_mode = LBM_GI_FULL;
+    int storage = LBM_STORAGE_F32;
+    int guard = 0;
+    lbm_side sides[4];
+    double Fx = 0, Fy = 0;
+    int Ly_option = 0;  // 0 = automatic
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t *d_solid = nullptr;
+    float *d_force = nullptr;
+    double *d_snap_ux = nullptr, *d_snap_uy = nullptr, *d_partials = nullptr, *d_result = nullptr;
+    unsigned long long *d_guard = nullptr;
+    double *h_result = nullptr;  // pinned, 5 doubles
+    int res_blocks = 1;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    long steps = 0, launches = 0;
+    int num_sms = 1;
+};
+
+namespace {
+
+size_t pop_bytes(const lbm_ctx *c) { return (size_t)9 * (size_t)c->plane * storage_bytes(c->storage); }
+
+StepParams make_params(const lbm_ctx *c)
+{
+    StepParams p;
+    memset(&p, 0, sizeof(p));
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.pitch = c->pitch;
+    p.plane = c->plane;
+    p.perx = c->sides[0].kind == LBM_SIDE_PERIODIC;
+    p.pery = c->sides[2].kind == LBM_SIDE_PERIODIC;
+    p.gi_mode = c->gi_mode;
+    p.guard = c->guard;
+    p.gamma = c->gamma;
+    p.w3 = c->omega[3];
+    p.w4 = c->omega[4];
+    p.w5 = c->omega[5];
+    p.w6 = c->omega[6];
+    p.w7 = c->omega[7];
+    p.w8 = c->omega[8];
+    for (int s = 0; s < 4; ++s) {
+        const bool moving = c->sides[s].kind == LBM_SIDE_MOVING_WALL;
+        p.side_u[s][0] = moving ? c->sides[s].ux : 0.0;
+        p.side_u[s][1] = moving ? c->sides[s].uy : 0.0;
+    }
+    p.Fx = c->Fx;
+    p.Fy = c->Fy;
+    p.force = c->d_force;
+    p.solid = c->d_solid;
+    p.guard_count = c->d_guard;
+    p.nstrips = (c->nx + BW - 1) / BW;
+    int bps = 1;
+    switch (c->storage) {
+    case LBM_STORAGE_F16: bps = blocks_per_sm_f16(c->gi_mode); break;
+    case LBM_STORAGE_BF16: bps = blocks_per_sm_bf16(c->gi_mode); break;
+    case LBM_STORAGE_F64: bps = blocks_per_sm_f64(c->gi_mode); break;
+    default: bps = blocks_per_sm_f32(c->gi_mode); break;
+    }
+    const int resident = c->num_sms * bps;
+    int Ly = c->Ly_option;
+    if (Ly <= 0) {
+        // about four items per resident block, segments of at least 2 rows
+        const int nseg = (4 * resident + p.nstrips - 1) / p.nstrips;
+        Ly = (c->ny + nseg - 1) / nseg;
+        if (Ly < 2) Ly = 2;
+    }
+    if (Ly > c->ny) Ly = c->ny;
+    p.Ly = Ly;
+    const int nseg = (c->ny + Ly - 1) / Ly;
+    p.nitems = p.nstrips * nseg;
+    return p;
+}
+
+int step_grid(const lbm_ctx *c, const StepParams &p)
+{
+    int bps = 1;
+    switch (c->storage) {
+    case LBM_STORAGE_F16: bps = blocks_per_sm_f16(c->gi_mode); break;
+    case LBM_STORAGE_BF16: bps = blocks_per_sm_bf16(c->gi_mode); break;
+    case LBM_STORAGE_F64: bps = blocks_per_sm_f64(c->gi_mode); break;
+    default: bps = blocks_per_sm_f32(c->gi_mode); break;
+    }
+    const int resident = c->num_sms * bps;
+    return p.nitems < resident ? p.nitems : resident;
+}
+
+cudaError_t launch_step(const lbm_ctx *c, const StepParams &p, int grid, const void *fin, void *fout)
+{
+    switch (c->storage) {
+    case LBM_STORAGE_F16: return launch_step_f16(p, fin, fout, grid, c->stream);
+    case LBM_STORAGE_BF16: return launch_step_bf16(p, fin, fout, grid, c->stream);
+    case LBM_STORAGE_F64: return launch_step_f64(p, fin, fout, grid, c->stream);
+    default: return launch_step_f32(p, fin, fout, grid, c->stream);
+    }
+}
+
+bool valid_omega(double w) { return w > 0.0 && w < 2.0 && isfinite(w); }
+
+lbm_status check_ctx(const lbm_ctx *c)
+{
+    if (!c) return fail(LBM_ERR_INVALID, "null context");
+    return LBM_OK;
+}
+
+void free_ctx(lbm_ctx *c)
+{
+    if (!c) return;
+    if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+    if (c->stream && c->stream != c->own_stream) cudaStreamSynchronize(c->stream);
+    dev_free(c->f[0]);
+    dev_free(c->f[1]);
+    dev_free(c->d_solid);
+    dev_free(c->d_force);
+    dev_free(c->d_snap_ux);
+    dev_free(c->d_snap_uy);
+    dev_free(c->d_partials);
+    dev_free(c->d_result);
+    dev_free(c->d_guard);
+    if (c->h_result) cudaFreeHost(c->h_result);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+lbm_status snapshot_reset(lbm_ctx *c)
+{
+    StepParams p = make_params(c);
+    LBM_CUDA(launch_residual(p, c->storage, c->f[c->cur], c->d_snap_ux, c->d_snap_uy, c->d_partials,
+                             c->res_blocks, c->d_result, c->stream));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_error.c_str(); }
+
+lbm_status lbm_set_allocator(const lbm_allocator *a)
+{
+    if (a && (!a->alloc || !a->release)) return fail(LBM_ERR_INVALID, "allocator needs alloc and release");
+    if (a) g_alloc = *a;
+    else g_alloc = lbm_allocator{nullptr, nullptr, nullptr};
+    return LBM_OK;
+}
+
+lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const lbm_boundaries *bnd,
+                      lbm_ctx **out)
+{
+    if (!out) return fail(LBM_ERR_INVALID, "out is null");
+    *out = nullptr;
+    if (nx < 3 || ny < 3) return fail(LBM_ERR_INVALID, "nx and ny must be >= 3");
+    if (ny > 65535) return fail(LBM_ERR_INVALID, "ny must be <= 65535");
+    if ((long long)nx * ny > (1LL << 31) / 9) return fail(LBM_ERR_INVALID, "domain too large");
+    if (!(nu > 0.0) || !isfinite(nu)) return fail(LBM_ERR_INVALID, "nu must be > 0");
+    if (!(gamma > 0.0 && gamma <= 1.0)) return fail(LBM_ERR_INVALID, "gamma must be in (0, 1]");
+    if (!(U >= 0.0) || !isfinite(U)) return fail(LBM_ERR_INVALID, "U must be >= 0");
+    const double w = 1.0 / (3.0 * nu / gamma + 0.5);
+    if (!valid_omega(w)) return fail(LBM_ERR_INVALID, "omega4 out of (0, 2)");
+
+    lbm_side sides[4];
+    if (bnd) {
+        sides[0] = bnd->west;
+        sides[1] = bnd->east;
+        sides[2] = bnd->south;
+        sides[3] = bnd->north;
+        for (int s = 0; s < 4; ++s)
+            if (sides[s].kind < 0 || sides[s].kind > 2) return fail(LBM_ERR_INVALID, "bad side kind");
+        if ((sides[0].kind == LBM_SIDE_PERIODIC) != (sides[1].kind == LBM_SIDE_PERIODIC) ||
+            (sides[2].kind == LBM_SIDE_PERIODIC) != (sides[3].kind == LBM_SIDE_PERIODIC))
+            return fail(LBM_ERR_INVALID, "opposite sides must both be periodic or both walls");
+    } else {
+        sides[0] = sides[1] = sides[2] = lbm_side{LBM_SIDE_WALL, 0.0, 0.0};
+        sides[3] = lbm_side{LBM_SIDE_MOVING_WALL, U, 0.0};
+    }
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(LBM_ERR_OOM, "host allocation failed");
+    c->nx = nx;
+    c->ny = ny;
+    c->pitch = (nx + 63) / 64 * 64;
+    c->plane = (long long)c->pitch * ny;
+    c->nu = nu;
+    c->gamma = gamma;
+    c->U = U;
+    c->omega[4] = c->omega[5] = w;
+    for (int s = 0; s < 4; ++s) c->sides[s] = sides[s];
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (c->num_sms < 1) c->num_sms = 1;
+
+    e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    c->stream = c->own_stream;
+    const size_t N = (size_t)nx * ny;
+    c->f[0] = dev_alloc(pop_bytes(c));
+    c->f[1] = dev_alloc(pop_bytes(c));
+    c->d_snap_ux = (double *)dev_alloc(N * sizeof(double));
+    c->d_snap_uy = (double *)dev_alloc(N * sizeof(double));
+    StepParams p0 = make_params(c);
+    c->res_blocks = residual_blocks(p0);
+    c->d_partials = (double *)dev_alloc((size_t)c->res_blocks * 5 * sizeof(double));
+    c->d_result = (double *)dev_alloc(8 * sizeof(double));
+    c->d_guard = (unsigned long long *)dev_alloc(sizeof(unsigned long long));
+    if (!c->f[0] || !c->f[1] || !c->d_snap_ux || !c->d_snap_uy || !c->d_partials || !c->d_result || !c->d_guard) {
+        free_ctx(c);
+        return fail(LBM_ERR_OOM, "device allocation failed");
+    }
+    if (cudaMallocHost((void **)&c->h_result, 8 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return fail(LBM_ERR_OOM, "pinned host allocation failed");
+    }
+    if (bnd && bnd->solid) {
+        c->d_solid = (uint8_t *)dev_alloc((size_t)c->pitch * ny);
+        if (!c->d_solid) {
+            free_ctx(c);
+            return fail(LBM_ERR_OOM, "device allocation failed (mask)");
+        }
+        std::vector<uint8_t> h((size_t)c->pitch * ny, 0);
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) h[(size_t)y * c->pitch + x] = bnd->solid[(size_t)y * nx + x] ? 1 : 0;
+        e = cudaMemcpy(c->d_solid, h.data(), h.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_ctx(c);
+            return cuda_fail(e, "cudaMemcpy(mask)");
+        }
+    }
+    e = cudaMemsetAsync(c->d_guard, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, pop_bytes(c), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_snap_ux, 0, N * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_snap_uy, 0, N * sizeof(double), c->stream);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return cuda_fail(e, "cudaMemset");
+    }
+    *out = c;
+    lbm_status s = lbm_init_fields(c, nullptr, nullptr, nullptr);
+    if (s != LBM_OK) {
+        free_ctx(c);
+        *out = nullptr;
+        return s;
+    }
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx) { free_ctx(ctx); }
+
+lbm_status lbm_set_stream(lbm_ctx *c, void *stream)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->own_stream;
+    if (s != c->stream) {
+        // order the new stream after everything queued on the old one
+        cudaEvent_t ev;
+        LBM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaEventRecord(ev, c->stream);
+        cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);
+        c->stream = s;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_option(lbm_ctx *c, const char *key, double v)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!key) return fail(LBM_ERR_INVALID, "null option key");
+    const std::string k(key);
+    if (k == "omega3" || k == "omega6" || k == "omega7" || k == "omega8") {
+        if (!valid_omega(v)) return fail(LBM_ERR_INVALID, k + " must be in (0, 2)");
+        c->omega[k[5] - '0'] = v;
+    } else if (k == "gi_mode") {
+        if (v != 0.0 && v != 1.0 && v != 2.0) return fail(LBM_ERR_INVALID, "gi_mode must be 0, 1 or 2");
+        c->gi_mode = (int)v;
+    } else if (k == "guard") {
+        c->guard = v != 0.0;
+    } else if (k == "fx" || k == "fy") {
+        if (!isfinite(v)) return fail(LBM_ERR_INVALID, "force must be finite");
+        (k == "fx" ? c->Fx : c->Fy) = v;
+    } else if (k == "cells_per_item") {
+        if (!(v >= 1.0) || v > 65535.0) return fail(LBM_ERR_INVALID, "cells_per_item must be >= 1");
+        c->Ly_option = (int)v;
+    } else if (k == "storage") {
+        const int ns = (int)v;
+        if (v != (double)ns || ns < 0 || ns > 3) return fail(LBM_ERR_INVALID, "storage must be 0..3");
+        if (ns == c->storage) return LBM_OK;
+        const int old = c->storage;
+        StepParams p = make_params(c);
+        c->storage = ns;
+        void *nf0 = dev_alloc(pop_bytes(c));
+        void *nf1 = dev_alloc(pop_bytes(c));
+        if (!nf0 || !nf1) {
+            dev_free(nf0);
+            dev_free(nf1);
+            c->storage = old;
+            return fail(LBM_ERR_OOM, "device allocation failed (storage change)");
+        }
+        cudaError_t e = launch_convert(p, old, c->f[c->cur], ns, nf0, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(nf1, 0, pop_bytes(c), c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            dev_free(nf0);
+            dev_free(nf1);
+            c->storage = old;
+            return cuda_fail(e, "storage conversion");
+        }
+        dev_free(c->f[0]);
+        dev_free(c->f[1]);
+        c->f[0] = nf0;
+        c->f[1] = nf1;
+        c->cur = 0;
+    } else {
+        return fail(LBM_ERR_INVALID, "unknown option: " + k);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_option(lbm_ctx *c, const char *key, double *v)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!key || !v) return fail(LBM_ERR_INVALID, "null argument");
+    const std::string k(key);
+    if (k.size() == 6 && k.compare(0, 5, "omega") == 0 && k[5] >= '3' && k[5] <= '8') *v = c->omega[k[5] - '0'];
+    else if (k == "gi_mode") *v = c->gi_mode;
+    else if (k == "guard") *v = c->guard;
+    else if (k == "fx") *v = c->Fx;
+    else if (k == "fy") *v = c->Fy;
+    else if (k == "storage") *v = c->storage;
+    else if (k == "gamma") *v = c->gamma;
+    else if (k == "nu") *v = c->nu;
+    else if (k == "cells_per_item") *v = make_params(c).Ly;
+    else if (k == "work_items") *v = make_params(c).nitems;
+    else if (k == "grid") {
+        StepParams p = make_params(c);
+        *v = step_grid(c, p);
+    } else if (k == "pitch") *v = c->pitch;
+    else return fail(LBM_ERR_INVALID, "unknown option: " + k);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force_field(lbm_ctx *c, const double *fx, const double *fy)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!fx && !fy) {
+        LBM_CUDA(cudaStreamSynchronize(c->stream));
+        dev_free(c->d_force);
+        c->d_force = nullptr;
+        return LBM_OK;
+    }
+    if (!fx || !fy) return fail(LBM_ERR_INVALID, "fx and fy must both be given");
+    if (!c->d_force) {
+        c->d_force = (float *)dev_alloc((size_t)2 * c->plane * sizeof(float));
+        if (!c->d_force) return fail(LBM_ERR_OOM, "device allocation failed (force)");
+    }
+    std::vector<float> h((size_t)2 * c->plane, 0.0f);
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x) {
+            h[(size_t)y * c->pitch + x] = (float)fx[(size_t)y * c->nx + x];
+            h[(size_t)c->plane + (size_t)y * c->pitch + x] = (float)fy[(size_t)y * c->nx + x];
+        }
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    LBM_CUDA(cudaMemcpy(c->d_force, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_ctx *c, const double *rho, const double *ux, const double *uy)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    const size_t N = (size_t)c->nx * c->ny;
+    const double *src[3] = {rho, ux, uy};
+    DevBuf b0(rho ? N * 8 : 0), b1(ux ? N * 8 : 0), b2(uy ? N * 8 : 0);
+    DevBuf *bufs[3] = {&b0, &b1, &b2};
+    const double *dptr[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i) {
+        if (!src[i]) continue;
+        if (!bufs[i]->p) return fail(LBM_ERR_OOM, "device allocation failed (init)");
+        LBM_CUDA(cudaMemcpyAsync(bufs[i]->p, src[i], N * 8, cudaMemcpyHostToDevice, c->stream));
+        dptr[i] = (const double *)bufs[i]->p;
+    }
+    StepParams p = make_params(c);
+    LBM_CUDA(launch_init_eq(p, c->storage, dptr[0], dptr[1], dptr[2], c->f[c->cur], c->stream));
+    lbm_status s = snapshot_reset(c);
+    if (s != LBM_OK) return s;
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    c->steps = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, long n)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (n < 0) return fail(LBM_ERR_INVALID, "n must be >= 0");
+    if (n == 0) return LBM_OK;
+    StepParams p = make_params(c);
+    const int grid = step_grid(c, p);
+    for (long i = 0; i < n; ++i) {
+        cudaError_t e = launch_step(c, p, grid, c->f[c->cur], c->f[1 - c->cur]);
+        if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
+        c->cur = 1 - c->cur;
+        c->steps += 1;
+        c->launches += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_ctx *c, double *residual, double sums[5])
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    lbm_status s = snapshot_reset(c);
+    if (s != LBM_OK) return s;
+    LBM_CUDA(cudaMemcpyAsync(c->h_result, c->d_result, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    const double du2 = c->h_result[0], u2 = c->h_result[1];
+    double r;
+    if (!isfinite(du2) || !isfinite(u2)) r = NAN;
+    else if (u2 == 0.0) r = du2 == 0.0 ? 0.0 : INFINITY;
+    else r = sqrt(du2 / u2);
+    if (residual) *residual = r;
+    if (sums)
+        for (int k = 0; k < 5; ++k) sums[k] = c->h_result[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_run_to_steady(lbm_ctx *c, double tol, long check_every, long max_steps, double wall_seconds,
+                             long *steps_done, double *final_residual)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!(tol > 0.0)) return fail(LBM_ERR_INVALID, "tol must be > 0");
+    if (check_every < 1) return fail(LBM_ERR_INVALID, "check_every must be >= 1");
+    if (max_steps < 0) return fail(LBM_ERR_INVALID, "max_steps must be >= 0");
+    const auto t0 = std::chrono::steady_clock::now();
+    long done = 0;
+    double r = INFINITY;
+    lbm_status st = LBM_ERR_NOT_CONVERGED;
+    // fresh snapshot at the starting state
+    lbm_status s = lbm_residual(c, nullptr, nullptr);
+    if (s != LBM_OK) return s;
+    while (done < max_steps) {
+        const long n = check_every < max_steps - done ? check_every : max_steps - done;
+        s = lbm_step(c, n);
+        if (s != LBM_OK) return s;
+        done += n;
+        s = lbm_residual(c, &r, nullptr);
+        if (s != LBM_OK) return s;
+        if (!isfinite(r)) {
+            st = fail(LBM_ERR_DIVERGED, "non-finite velocity after step " + std::to_string(c->steps));
+            break;
+        }
+        if (r < tol) {
+            st = LBM_OK;
+            break;
+        }
+        if (wall_seconds > 0.0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > wall_seconds) {
+                st = fail(LBM_ERR_TIMEOUT, "wall-clock limit reached");
+                break;
+            }
+        }
+    }
+    if (st == LBM_ERR_NOT_CONVERGED) fail(st, "max_steps reached with residual " + std::to_string(r));
+    if (steps_done) *steps_done = done;
+    if (final_residual) *final_residual = r;
+    return st;
+}
+
+lbm_status lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    const size_t N = (size_t)c->nx * c->ny;
+    DevBuf b(3 * N * sizeof(double));
+    if (!b.p) return fail(LBM_ERR_OOM, "device allocation failed (fields)");
+    double *d = (double *)b.p;
+    StepParams p = make_params(c);
+    LBM_CUDA(launch_fields(p, c->storage, c->f[c->cur], d, d + N, d + 2 * N, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (rho) LBM_CUDA(cudaMemcpy(rho, d, N * 8, cudaMemcpyDeviceToHost));
+    if (ux) LBM_CUDA(cudaMemcpy(ux, d + N, N * 8, cudaMemcpyDeviceToHost));
+    if (uy) LBM_CUDA(cudaMemcpy(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx *c, double *f)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!f) return fail(LBM_ERR_INVALID, "null output");
+    const size_t N = (size_t)c->nx * c->ny;
+    DevBuf b(9 * N * sizeof(double));
+    if (!b.p) return fail(LBM_ERR_OOM, "device allocation failed (populations)");
+    StepParams p = make_params(c);
+    LBM_CUDA(launch_pops_to_f64(p, c->storage, c->f[c->cur], (double *)b.p, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    LBM_CUDA(cudaMemcpy(f, b.p, 9 * N * 8, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!f) return fail(LBM_ERR_INVALID, "null input");
+    const size_t N = (size_t)c->nx * c->ny;
+    DevBuf b(9 * N * sizeof(double));
+    if (!b.p) return fail(LBM_ERR_OOM, "device allocation failed (populations)");
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    LBM_CUDA(cudaMemcpy(b.p, f, 9 * N * 8, cudaMemcpyHostToDevice));
+    StepParams p = make_params(c);
+    LBM_CUDA(launch_pops_from_f64(p, c->storage, (const double *)b.p, c->f[c->cur], c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_steps_done(lbm_ctx *c, long *steps)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!steps) return fail(LBM_ERR_INVALID, "null output");
+    *steps = c->steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_kernel_launches(lbm_ctx *c, long *launches)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!launches) return fail(LBM_ERR_INVALID, "null output");
+    *launches = c->launches;
+    return LBM_OK;
+}
+
+lbm_status lbm_guard_count(lbm_ctx *c, long *count)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!count) return fail(LBM_ERR_INVALID, "null output");
+    unsigned long long v = 0;
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    LBM_CUDA(cudaMemcpy(&v, c->d_guard, sizeof(v), cudaMemcpyDeviceToHost));
+    *count = (long)v;
+    return LBM_OK;
+}
+
+// Checkpoint layout: 8-byte magic, then int32 {version, nx, ny, storage, gi_mode},
+// int64 steps, double {gamma, nu, omega3..8, Fx, Fy}, then nine planes of
+// nx*ny stored elements (rows packed).
+static const char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
+
+lbm_status lbm_save(lbm_ctx *c, const char *path)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!path) return fail(LBM_ERR_INVALID, "null path");
+    const size_t es = storage_bytes(c->storage);
+    std::vector<unsigned char> h((size_t)9 * c->nx * c->ny * es);
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    LBM_CUDA(cudaMemcpy2D(h.data(), (size_t)c->nx * es, c->f[c->cur], (size_t)c->pitch * es, (size_t)c->nx * es,
+                          (size_t)9 * c->ny, cudaMemcpyDeviceToHost));
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    int hdr[5] = {1, c->nx, c->ny, c->storage, c->gi_mode};
+    long long steps = c->steps;
+    double par[10] = {c->gamma, c->nu, c->omega[3], c->omega[4], c->omega[5], c->omega[6], c->omega[7], c->omega[8], c->Fx, c->Fy};
+    bool ok = fwrite(kMagic, 1, 8, fp) == 8 && fwrite(hdr, sizeof(int), 5, fp) == 5 &&
+              fwrite(&steps, sizeof(steps), 1, fp) == 1 && fwrite(par, sizeof(double), 10, fp) == 10 &&
+              fwrite(h.data(), 1, h.size(), fp) == h.size();
+    ok = (fclose(fp) == 0) && ok;
+    if (!ok) return fail(LBM_ERR_IO, std::string("write failed: ") + path);
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx *c, const char *path)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!path) return fail(LBM_ERR_INVALID, "null path");
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
+    char magic[8];
+    int hdr[5];
+    long long steps;
+    double par[10];
+    bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, kMagic, 8) == 0 &&
+              fread(hdr, sizeof(int), 5, fp) == 5 && fread(&steps, sizeof(steps), 1, fp) == 1 &&
+              fread(par, sizeof(double), 10, fp) == 10;
+    if (!ok || hdr[0] != 1) {
+        fclose(fp);
+        return fail(LBM_ERR_IO, "not a checkpoint of this library");
+    }
+    if (hdr[1] != c->nx || hdr[2] != c->ny) {
+        fclose(fp);
+        return fail(LBM_ERR_INVALID, "checkpoint size differs from the context");
+    }
+    if (hdr[3] < 0 || hdr[3] > 3 || hdr[4] < 0 || hdr[4] > 2) {
+        fclose(fp);
+        return fail(LBM_ERR_IO, "corrupt checkpoint header");
+    }
+    lbm_status s = lbm_set_option(c, "storage", hdr[3]);
+    if (s != LBM_OK) {
+        fclose(fp);
+        return s;
+    }
+    const size_t es = storage_bytes(c->storage);
+    std::vector<unsigned char> h((size_t)9 * c->nx * c->ny * es);
+    ok = fread(h.data(), 1, h.size(), fp) == h.size();
+    fclose(fp);
+    if (!ok) return fail(LBM_ERR_IO, "truncated checkpoint");
+    c->gi_mode = hdr[4];
+    c->gamma = par[0];
+    c->nu = par[1];
+    for (int k = 0; k < 6; ++k) c->omega[3 + k] = par[2 + k];
+    c->Fx = par[8];
+    c->Fy = par[9];
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    LBM_CUDA(cudaMemcpy2D(c->f[c->cur], (size_t)c->pitch * es, h.data(), (size_t)c->nx * es, (size_t)c->nx * es,
+                          (size_t)9 * c->ny, cudaMemcpyHostToDevice));
+    c->steps = (long)steps;
+    return snapshot_reset(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+// Auxiliary kernels: equilibrium initialisation, observed fields, the FP64
+// convergence residual, and population format conversions.
+#include <math.h>
+
+#include "d2q9_collide.cuh"
+
+namespace lbm {
+
+size_t storage_bytes(int storage)
+{
+    switch (storage) {
+    case LBM_STORAGE_F16:
+    case LBM_STORAGE_BF16: return 2;
+    case LBM_STORAGE_F64: return 8;
+    default: return 4;
+    }
+}
+
+// Generic element access in FP64 for the one-off kernels below.
+__device__ __forceinline__ double load_any(const void *f, int storage, size_t i)
+{
+    switch (storage) {
+    case LBM_STORAGE_F16: return (double)__half2float(static_cast<const __half *>(f)[i]);
+    case LBM_STORAGE_BF16: return (double)__bfloat162float(static_cast<const __nv_bfloat16 *>(f)[i]);
+    case LBM_STORAGE_F64: return static_cast<const double *>(f)[i];
+    default: return (double)static_cast<const float *>(f)[i];
+    }
+}
+
+__device__ __forceinline__ void store_any(void *f, int storage, size_t i, double v)
+{
+    switch (storage) {
+    case LBM_STORAGE_F16: static_cast<__half *>(f)[i] = __double2half(v); break;
+    case LBM_STORAGE_BF16: static_cast<__nv_bfloat16 *>(f)[i] = __double2bfloat16(v); break;
+    case LBM_STORAGE_F64: static_cast<double *>(f)[i] = v; break;
+    default: static_cast<float *>(f)[i] = (float)v; break;
+    }
+}
+
+__device__ __forceinline__ bool solid_at(const StepParams &p, int x, int y)
+{
+    return p.solid != nullptr && p.solid[(size_t)y * p.pitch + x] != 0;
+}
+
+__device__ __forceinline__ void force_at(const StepParams &p, int x, int y, double &Fx, double &Fy)
+{
+    if (p.force) {
+        const size_t i = (size_t)y * p.pitch + x;
+        Fx = p.force[i];
+        Fy = p.force[(size_t)p.plane + i];
+    } else {
+        Fx = p.Fx;
+        Fy = p.Fy;
+    }
+}
+
+// Inverse of the Eq. 5 map for the moment order
+// (k0, kx, ky, kxx, kyy, kxy, kxxy, kxyy, kxxyy).
+__device__ __forceinline__ void pops_from_raw(const double (&k)[9], double (&f)[9])
+{
+    f[0] = k[0] - k[3] - k[4] + k[8];
+    f[1] = 0.5 * (k[1] + k[3] - k[7] - k[8]);
+    f[3] = 0.5 * (-k[1] + k[3] + k[7] - k[8]);
+    f[2] = 0.5 * (k[2] + k[4] - k[6] - k[8]);
+    f[4] = 0.5 * (-k[2] + k[4] + k[6] - k[8]);
+    f[5] = 0.25 * (k[5] + k[6] + k[7] + k[8]);
+    f[6] = 0.25 * (-k[5] + k[6] - k[7] + k[8]);
+    f[7] = 0.25 * (k[5] - k[6] - k[7] + k[8]);
+    f[8] = 0.25 * (-k[5] - k[6] + k[7] + k[8]);
+}
+
+// f~0 = f_eq(rho, u) - S/2 stored as deviations from w (rho0 = 1).  Raw
+// equilibria of Eq. 15 with the gamma^2 cubic terms; the fourth moment makes
+// the central fourth moment rho/9.
+__global__ void init_eq_kernel(const StepParams p, int storage, const double *rho_in,
+                               const double *ux_in, const double *uy_in, void *f)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const size_t ic = (size_t)y * p.nx + x;
+    const double r = rho_in ? rho_in[ic] : 1.0;
+    const double u = ux_in ? ux_in[ic] : 0.0;
+    const double v = uy_in ? uy_in[ic] : 0.0;
+    const double g = p.gamma;
+    double k[9] = {r,
+                   r * u,
+                   r * v,
+                   r / 3.0 + r * u * u / g,
+                   r / 3.0 + r * v * v / g,
+                   r * u * v / g,
+                   r * v / 3.0 + r * u * u * v / (g * g),
+                   r * u / 3.0 + r * u * v * v / (g * g),
+                   r / 9.0 + r * (u * u + v * v) / 3.0 + r * u * u * v * v * (3.0 - 6.0 / g + 4.0 / (g * g))};
+    double feq[9], S[9];
+    pops_from_raw(k, feq);
+    double Fx, Fy;
+    force_at(p, x, y, Fx, Fy);
+    double s[9] = {0.0,
+                   Fx / g,
+                   Fy / g,
+                   2.0 * Fx * u / (g * g),
+                   2.0 * Fy * v / (g * g),
+                   (Fx * v + Fy * u) / (g * g),
+                   Fy * u * u + 2.0 * Fx * u * v,
+                   Fx * v * v + 2.0 * Fy * v * u,
+                   2.0 * (Fx * u * v * v + Fy * v * u * u)};
+    pops_from_raw(s, S);
+    const size_t i = (size_t)y * p.pitch + x;
+    for (int a = 0; a < 9; ++a)
+        store_any(f, storage, (size_t)a * p.plane + i, feq[a] - weight(a) - 0.5 * S[a]);
+}
+
+cudaError_t launch_init_eq(const StepParams &p, int storage, const double *rho, const double *ux,
+                           const double *uy, void *f, cudaStream_t s)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    init_eq_kernel<<<grid, 128, 0, s>>>(p, storage, rho, ux, uy, f);
+    return cudaGetLastError();
+}
+
+// Observed fields: rho = 1 + sum g~, rho u = sum g~ e - F/(2 gamma); NaN in solids.
+__device__ __forceinline__ void local_fields(const StepParams &p, int storage, const void *f, int x,
+                                             int y, double &rho, double &ux, double &uy)
+{
+    const size_t i = (size_t)y * p.pitch + x;
+    double s = 0.0, jx = 0.0, jy = 0.0;
+    for (int a = 0; a < 9; ++a) {
+        const double ga = load_any(f, storage, (size_t)a * p.plane + i);
+        s += ga;
+        jx += ga * cx(a);
+        jy += ga * cy(a);
+    }
+    double Fx, Fy;
+    force_at(p, x, y, Fx, Fy);
+    rho = 1.0 + s;
+    ux = (jx - 0.5 * Fx / p.gamma) / rho;
+    uy = (jy - 0.5 * Fy / p.gamma) / rho;
+}
+
+__global__ void fields_kernel(const StepParams p, int storage, const void *f, double *rho, double *ux,
+                              double *uy)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const size_t o = (size_t)y * p.nx + x;
+    double r, u, v;
+    if (solid_at(p, x, y)) {
+        r = u = v = nan("");
+    } else {
+        local_fields(p, storage, f, x, y, r, u, v);
+    }
+    if (rho) rho[o] = r;
+    if (ux) ux[o] = u;
+    if (uy) uy[o] = v;
+}
+
+cudaError_t launch_fields(const StepParams &p, int storage, const void *f, double *rho, double *ux,
+                          double *uy, cudaStream_t s)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    fields_kernel<<<grid, 128, 0, s>>>(p, storage, f, rho, ux, uy);
+    return cudaGetLastError();
+}
+
+// ---- FP64 convergence residual ------------------------------------------------
+// Pass 1: each block accumulates {sum|du|^2, sum|u|^2, sum rho, sum rho ux,
+// sum rho uy} over a grid-stride range of fluid cells, reduces in FP64 with warp
+// shuffles and writes one row of `partials`; the velocity snapshot is replaced.
+// Pass 2: one block reduces the rows in a fixed order (deterministic).
+constexpr int RES_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum5(double (&v)[5], double *out)
+{
+    __shared__ double sh[NT / 32][5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+        for (int k = 0; k < 5; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double t = lane < NT / 32 ? sh[lane][k] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) out[k] = t;
+        }
+    }
+}
+
+__global__ void residual_pass1(const StepParams p, int storage, const void *f, double *snap_ux,
+                               double *snap_uy, double *partials)
+{
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const size_t N = (size_t)p.nx * p.ny;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % p.nx), y = (int)(c / p.nx);
+        if (solid_at(p, x, y)) continue;
+        double r, u, v;
+        local_fields(p, storage, f, x, y, r, u, v);
+        const double du = u - snap_ux[c], dv = v - snap_uy[c];
+        acc[0] += du * du + dv * dv;
+        acc[1] += u * u + v * v;
+        acc[2] += r;
+        acc[3] += r * u;
+        acc[4] += r * v;
+        snap_ux[c] = u;
+        snap_uy[c] = v;
+    }
+    block_sum5<RES_THREADS>(acc, partials + (size_t)blockIdx.x * 5);
+}
+
+__global__ void residual_pass2(const double *partials, int nrows, double *result)
+{
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x)
+        for (int k = 0; k < 5; ++k) acc[k] += partials[(size_t)r * 5 + k];
+    block_sum5<RES_THREADS>(acc, result);
+}
+
+int residual_blocks(const StepParams &p)
+{
+    const size_t N = (size_t)p.nx * p.ny;
+    size_t b = (N + RES_THREADS - 1) / RES_THREADS;
+    return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+}
+
+cudaError_t launch_residual(const StepParams &p, int storage, const void *f, double *snap_ux,
+                            double *snap_uy, double *partials, int nblocks, double *result,
+                            cudaStream_t s)
+{
+    residual_pass1<<<nblocks, RES_THREADS, 0, s>>>(p, storage, f, snap_ux, snap_uy, partials);
+    residual_pass2<<<1, RES_THREADS, 0, s>>>(partials, nblocks, result);
+    return cudaGetLastError();
+}
+
+// ---- format conversions ------------------------------------------------------
+__global__ void convert_kernel(const StepParams p, int from, const void *fin, int to, void *fout)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const size_t i = (size_t)y * p.pitch + x;
+    for (int a = 0; a < 9; ++a)
+        store_any(fout, to, (size_t)a * p.plane + i, load_any(fin, from, (size_t)a * p.plane + i));
+}
+
+cudaError_t launch_convert(const StepParams &p, int from_storage, const void *fin, int to_storage,
+                           void *fout, cudaStream_t s)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    convert_kernel<<<grid, 128, 0, s>>>(p, from_storage, fin, to_storage, fout);
+    return cudaGetLastError();
+}
+
+__global__ void to_f64_kernel(const StepParams p, int storage, const void *f, double *out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const size_t i = (size_t)y * p.pitch + x;
+    const size_t N = (size_t)p.nx * p.ny, o = (size_t)y * p.nx + x;
+    for (int a = 0; a < 9; ++a) out[(size_t)a * N + o] = load_any(f, storage, (size_t)a * p.plane + i) + weight(a);
+}
+
+__global__ void from_f64_kernel(const StepParams p, int storage, const double *in, void *f)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const size_t i = (size_t)y * p.pitch + x;
+    const size_t N = (size_t)p.nx * p.ny, o = (size_t)y * p.nx + x;
+    for (int a = 0; a < 9; ++a) store_any(f, storage, (size_t)a * p.plane + i, in[(size_t)a * N + o] - weight(a));
+}
+
+cudaError_t launch_pops_to_f64(const StepParams &p, int storage, const void *f, double *out, cudaStream_t s)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    to_f64_kernel<<<grid, 128, 0, s>>>(p, storage, f, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pops_from_f64(const StepParams &p, int storage, const double *in, void *f, cudaStream_t s)
+{
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    from_f64_kernel<<<grid, 128, 0, s>>>(p, storage, in, f);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

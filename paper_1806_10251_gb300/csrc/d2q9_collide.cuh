@@ -1,0 +1,212 @@
+// D2Q9 lattice, storage conversion and the cascaded central-moment collision of
+// the GI preconditioned scheme (Hajabdollahi & Premnath, arXiv 1806.10251),
+// written for register-resident evaluation in FP32 (FP64 for the FP64 format).
+//
+// Populations are handled as deviations g = f - w rho0 (rho0 = 1) from the rest
+// state: raw moments of f are then the rest-state moments plus those of g, and
+// every O(1) constant cancels analytically before any rounding happens.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Velocity ordering: 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1)
+//                    5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)
+__host__ __device__ constexpr int cx(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
+__host__ __device__ constexpr int cy(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
+// opposite directions
+__host__ __device__ constexpr int opposite(int a)
+{
+    return a == 0 ? 0 : a == 1 ? 3 : a == 2 ? 4 : a == 3 ? 1 : a == 4 ? 2 : a == 5 ? 7 : a == 6 ? 8 : a == 7 ? 5 : 6;
+}
+// lattice weights: 4/9, 1/9 (axis), 1/36 (diagonal)
+__host__ __device__ constexpr double weight(int a) { return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+// ---- storage conversion ------------------------------------------------------
+template <typename ST> struct StorageTraits;
+template <> struct StorageTraits<float> {
+    using R = float;
+    __device__ static __forceinline__ float load(const float *p) { return __ldg(p); }
+    __device__ static __forceinline__ void store(float *p, float v) { *p = v; }
+};
+template <> struct StorageTraits<double> {
+    using R = double;
+    __device__ static __forceinline__ double load(const double *p) { return __ldg(p); }
+    __device__ static __forceinline__ void store(double *p, double v) { *p = v; }
+};
+template <> struct StorageTraits<__half> {
+    using R = float;
+    __device__ static __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct StorageTraits<__nv_bfloat16> {
+    using R = float;
+    __device__ static __forceinline__ float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---- per-launch constants in the compute precision ---------------------------
+template <typename R>
+struct Consts {
+    R ig, half_ig;                 // 1/gamma, 1/(2 gamma)
+    R ig2;                         // 1/gamma^2
+    R w3_12, w4_4, w5_4, w6_4, w7_4, w8_4;
+    R c6;                          // third-order factor: 2 (Eq. 4) or 3/g - 1/g^2 (Sec. 5)
+    R A, B, C3;                    // A_gamma, B_gamma, C_gamma/3 (after Eq. 53)
+    R k3, k4, k5;                  // 1/omega_j - 1/2
+    R a3, a4;                      // 2/(3 omega3), 2/(3 omega4)
+
+    __device__ __forceinline__ void init(const StepParams &p)
+    {
+        const double g = p.gamma;
+        ig = R(1.0 / g);
+        half_ig = R(0.5 / g);
+        ig2 = R(1.0 / (g * g));
+        w3_12 = R(p.w3 / 12.0);
+        w4_4 = R(p.w4 / 4.0);
+        w5_4 = R(p.w5 / 4.0);
+        w6_4 = R(p.w6 / 4.0);
+        w7_4 = R(p.w7 / 4.0);
+        w8_4 = R(p.w8 / 4.0);
+        c6 = p.gi_mode == LBM_GI_UNCORRECTED ? R(2.0) : R(3.0 / g - 1.0 / (g * g));
+        A = R(4.0 / (g * g) - 1.0 / g);
+        B = R(1.0 / (g * g) - 1.0 / g);
+        C3 = R((1.0 / g - 1.0) / 3.0);
+        k3 = R(1.0 / p.w3 - 0.5);
+        k4 = R(1.0 / p.w4 - 0.5);
+        k5 = R(1.0 / p.w5 - 0.5);
+        a3 = R(2.0 / (3.0 * p.w3));
+        a4 = R(2.0 / (3.0 * p.w4));
+    }
+};
+
+// One cell: g holds the post-streaming deviations gbar on entry and the
+// post-collision deviations on exit (Eq. 2a: f~ = fbar + K g^ + S).
+// drx, dry: density gradient (used by the full kernel only).
+template <typename R, int MODE>
+__device__ __forceinline__ void collide_cell(R (&g)[9], R drx, R dry, R Fx, R Fy, bool forced,
+                                             const Consts<R> &c, bool guard,
+                                             unsigned long long *guard_count)
+{
+    const R third = R(1.0 / 3.0);
+    // conserved moments (Eq. 3 on gbar; rho = 1 + sum g)
+    const R kxxyy = (g[5] + g[6]) + (g[7] + g[8]);
+    const R kxx = (g[1] + g[3]) + kxxyy;
+    const R kyy = (g[2] + g[4]) + kxxyy;
+    const R dr = g[0] + (g[1] + g[3]) + (g[2] + g[4]) + kxxyy;
+    const R rho = R(1) + dr;
+    const R irho = R(1) / rho;
+    const R jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const R jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    // velocity with the forcing shift: rho u = sum fbar e + F/(2 gamma)
+    const R ux = (jx + Fx * c.half_ig) * irho;
+    const R uy = (jy + Fy * c.half_ig) * irho;
+    // remaining raw moments of gbar (xy, xxy, xyy)
+    const R kxy = (g[5] + g[7]) - (g[6] + g[8]);
+    const R kxxy = (g[5] + g[6]) - (g[7] + g[8]);
+    const R kxyy = (g[5] + g[8]) - (g[6] + g[7]);
+
+    const R ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+
+    // preconditioned source raw moments (list after Eq. 15)
+    R sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0, sxxy = 0, sxyy = 0, sxxyy = 0;
+    if (forced) {
+        sx = Fx * c.ig;
+        sy = Fy * c.ig;
+        sxx = R(2) * Fx * ux * c.ig2;
+        syy = R(2) * Fy * uy * c.ig2;
+        sxy = (Fx * uy + Fy * ux) * c.ig2;
+        sxxy = Fy * ux2 + R(2) * Fx * uxy;
+        sxyy = Fx * uy2 + R(2) * Fy * uxy;
+        sxxyy = R(2) * (Fx * ux * uy2 + Fy * uy * ux2);
+    }
+
+    // extended-equilibrium corrections (Eq. 33 with Eqs. 45-47)
+    R M3 = 0, M4 = 0, M5 = 0;
+    if (MODE == LBM_GI_FULL) {
+        // second-order non-equilibrium moments of f = fbar + S/2
+        const R m3 = (kxx + kyy + R(0.5) * (sxx + syy)) - (R(2.0 / 3.0) * dr + rho * (ux2 + uy2) * c.ig);
+        const R m4 = (kxx - kyy + R(0.5) * (sxx - syy)) - rho * (ux2 - uy2) * c.ig;
+        const R Aux2 = c.A * ux2, Auy2 = c.A * uy2, Bux2 = c.B * ux2, Buy2 = c.B * uy2;
+        const R P = R(-0.5) * (Aux2 + Buy2), Q = R(-0.5) * (Auy2 + Bux2);
+        const R Pt = R(-0.5) * (Aux2 - Buy2), Qt = R(-0.5) * (Auy2 - Bux2);
+        // Eq. 53
+        R c1 = (c.a3 + P) * rho, c2 = (c.a3 + Q) * rho;
+        R c1t = (c.a4 + Pt) * rho, c2t = (c.a4 + Qt) * rho;
+        R D = -c1 * c2t - c1t * c2;
+        if (guard) {
+            const R D0 = R(-2) * (c.a3 * rho) * (c.a4 * rho);
+            if (fabs(D) < R(0.1) * fabs(D0)) {
+                c1 = c2 = c.a3 * rho;
+                c1t = c2t = c.a4 * rho;
+                D = -c1 * c2t - c1t * c2;
+                if (guard_count) atomicAdd(guard_count, 1ull);
+            }
+        }
+        // Eq. 54
+        const R er = c.C3 * (ux * drx + uy * dry);
+        const R ert = c.C3 * (ux * drx - uy * dry);
+        const R R3 = m3 - er, R4 = m4 - ert;
+        const R iD = R(1) / D;
+        // Eq. 55a, and 55b with the c~1 term's sign as the solve of Eqs. 51-52 gives it
+        const R dux = (c2t * R3 + c2 * R4) * iD;
+        const R duy = (c1t * R3 - c1 * R4) * iD;
+        // Eq. 45: th3x = 2 k3 rho P, th3y = 2 k3 rho Q, (la3x, la3y) = -(2/3) k3 C (ux, uy)
+        M3 = R(2) * c.k3 * (rho * (P * dux + Q * duy) - er);
+        // Eq. 46: th4x = 2 k4 rho P~, th4y = 2 k4 rho Q~, (la4x, la4y) = -(2/3) k4 C (ux, uy)
+        M4 = R(2) * c.k4 * (rho * (Pt * dux - Qt * duy) - ert);
+        // Eq. 47: th5x = th5y = -k5 rho B ux uy, (la5x, la5y) = -(1/3) k5 C (uy, ux)
+        M5 = -c.k5 * (rho * c.B * uxy * (dux + duy) + c.C3 * (uy * drx + ux * dry));
+    }
+
+    // cascaded collision (Sec. 5; Eq. 4 bars and source terms kept)
+    const R g3 = c.w3_12 * (R(2.0 / 3.0) * dr + rho * (ux2 + uy2) * c.ig - (kxx + kyy)
+                            - R(0.5) * (sxx + syy) + M3);
+    const R g4 = c.w4_4 * (rho * (ux2 - uy2) * c.ig - (kxx - kyy) - R(0.5) * (sxx - syy) + M4);
+    const R g5 = c.w5_4 * (rho * uxy * c.ig - kxy - R(0.5) * sxy + M5);
+    const R t34p = R(3) * g3 + g4, t34m = R(3) * g3 - g4;
+    const R g6 = c.w6_4 * (c.c6 * rho * ux2 * uy + kxxy - R(2) * ux * kxy - uy * (third + kxx) - R(0.5) * sxxy)
+               - R(0.5) * uy * t34p - R(2) * ux * g5;
+    const R g7 = c.w7_4 * (c.c6 * rho * ux * uy2 + kxyy - R(2) * uy * kxy - ux * (third + kyy) - R(0.5) * sxyy)
+               - R(0.5) * ux * t34m - R(2) * uy * g5;
+    const R g8 = c.w8_4 * (dr * R(1.0 / 9.0) + R(3) * rho * ux2 * uy2
+                           - (kxxyy - R(2) * ux * kxyy - R(2) * uy * kxxy + ux2 * (third + kyy)
+                              + uy2 * (third + kxx) + R(4) * uxy * kxy)
+                           - R(0.5) * sxxyy)
+               - R(2) * g3 - R(0.5) * uy2 * t34p - R(0.5) * ux2 * t34m - R(4) * uxy * g5
+               - R(2) * uy * g6 - R(2) * ux * g7;
+
+    // f~ = fbar + K g^ (columns: K3 = 3|e^2| - 4, K4 = |ex^2 - ey^2|, K5 = |ex ey|,
+    // K6 = -3|ex^2 ey| + 2|ey|, K7 = -3|ex ey^2| + 2|ex|, K8 = 9|ex^2 ey^2| - 6|e^2| + 4)
+    const R d8 = R(2) * g8;
+    g[0] += R(4) * (g8 - g3);
+    g[1] += -g3 + g4 + R(2) * g7 - d8;
+    g[2] += -g3 - g4 + R(2) * g6 - d8;
+    g[3] += -g3 + g4 - R(2) * g7 - d8;
+    g[4] += -g3 - g4 - R(2) * g6 - d8;
+    const R h = R(2) * g3 + g8;
+    g[5] += h + g5 - g6 - g7;
+    g[6] += h - g5 - g6 + g7;
+    g[7] += h + g5 + g6 + g7;
+    g[8] += h - g5 + g6 - g7;
+
+    if (forced) {
+        // S = T^-1 sigma' (inverse of the Eq. 5 map), sigma'_0 = 0
+        g[0] += -sxx - syy + sxxyy;
+        g[1] += R(0.5) * (sx + sxx - sxyy - sxxyy);
+        g[3] += R(0.5) * (-sx + sxx + sxyy - sxxyy);
+        g[2] += R(0.5) * (sy + syy - sxxy - sxxyy);
+        g[4] += R(0.5) * (-sy + syy + sxxy - sxxyy);
+        g[5] += R(0.25) * (sxy + sxxy + sxyy + sxxyy);
+        g[6] += R(0.25) * (-sxy + sxxy - sxyy + sxxyy);
+        g[7] += R(0.25) * (sxy - sxxy - sxyy + sxxyy);
+        g[8] += R(0.25) * (-sxy - sxxy + sxyy + sxxyy);
+    }
+}
+
+}  // namespace lbm

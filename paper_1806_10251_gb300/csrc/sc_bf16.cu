@@ -1,0 +1,13 @@
+// Step kernel instantiations for the __nv_bfloat16 population storage.
+#include "stream_collide.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step_bf16(const StepParams &p, const void *fin, void *fout, int grid, cudaStream_t s)
+{
+    return launch_step_t<__nv_bfloat16>(p, fin, fout, grid, s);
+}
+
+int blocks_per_sm_bf16(int gi_mode) { return blocks_per_sm_t<__nv_bfloat16>(gi_mode); }
+
+}  // namespace lbm

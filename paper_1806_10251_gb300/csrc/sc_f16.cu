@@ -1,0 +1,13 @@
+// Step kernel instantiations for the __half population storage.
+#include "stream_collide.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step_f16(const StepParams &p, const void *fin, void *fout, int grid, cudaStream_t s)
+{
+    return launch_step_t<__half>(p, fin, fout, grid, s);
+}
+
+int blocks_per_sm_f16(int gi_mode) { return blocks_per_sm_t<__half>(gi_mode); }
+
+}  // namespace lbm

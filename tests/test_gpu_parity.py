@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Small and ragged domains are compared element by element after many steps;
+the full-size 4096 x 4096 cavity is compared on sampled windows: the oracle
+takes the GPU's state after step n-1 on a window plus a two-cell margin (the
+dependency radius of one step: one cell for streaming, one more for the
+density gradient), advances it once, and the window's interior must match the
+GPU's step n.
+
+Tolerances (FP32 storage and collision): populations to 2e-6 absolute, and the
+spec bound max|du|/U <= 1e-5 after 1000 steps of the 128 x 128 cavity.
+FP64 storage: 1e-12.  FP16/BF16 storage: stated per test.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+import workloads as wl
+from paper_1806_10251_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def oracle_for(case, gi_mode=orc.GI_FULL, **kw):
+    d = orc.Domain(case.nx, case.ny, case.nu, case.gamma, case.sides, gi_mode=gi_mode, solid=case.solid,
+                   Fx=case.Fx, Fy=case.Fy, **kw)
+    if case.force_x is not None:
+        d.set_force_field(case.force_x, case.force_y)
+    d.init_equilibrium(case.rho0, case.ux0, case.uy0)
+    return d
+
+
+def fluid(case):
+    return np.ones((case.ny, case.nx), bool) if case.solid is None else case.solid == 0
+
+
+def compare(case, steps, gi_mode=orc.GI_FULL, storage=lbm.STORAGE_F32, pop_tol=2e-6, **opts):
+    g = lbm.solver_from_case(case, gi_mode=gi_mode, storage=storage, **opts)
+    o = oracle_for(case, gi_mode)
+    g.step(steps)
+    o.step(steps)
+    fg, fo = g.populations(), o.pops()
+    m = fluid(case)
+    dpop = np.abs(fg - fo)[:, m].max()
+    rg, ug, vg = g.fields()
+    ro, uo, vo = o.fields()
+    du = max(np.abs(ug - uo)[m].max(), np.abs(vg - vo)[m].max())
+    assert dpop < pop_tol, (case.name, dpop)
+    return dpop, du, (rg, ug, vg), (ro, uo, vo)
+
+
+@pytest.mark.parametrize("gi_mode", [0, 1, 2])
+def test_random_periodic_ragged(gi_mode):
+    # 300 x 41: three strips (the last ragged) and several row segments
+    c = wl.random_periodic(300, 41, 0.45, 0.03, seed=11)
+    compare(c, 60, gi_mode)
+
+
+@pytest.mark.parametrize("gi_mode", [0, 2])
+def test_random_cavity_walls_and_lid(gi_mode):
+    c = wl.random_cavity_state(200, 37, 0.5, Re=80.0, seed=5)
+    compare(c, 120, gi_mode)
+
+
+def test_cavity_128_1000_steps_north_star_bound():
+    """128 x 128 lid-driven cavity, Re = 100, gamma = 0.5, from rest: after 1000
+    steps max |du| / U <= 1e-5."""
+    c = wl.cavity(128, 100.0, 0.1, 0.5)
+    dpop, du, *_ = compare(c, 1000)
+    assert du / c.U <= 1e-5, du / c.U
+
+
+def test_small_and_degenerate_sizes():
+    for nx, ny in ((3, 3), (5, 4), (129, 3), (3, 130), (127, 9)):
+        c = wl.random_cavity_state(nx, ny, 0.6, Re=20.0, seed=nx * ny)
+        compare(c, 25)
+        c = wl.random_periodic(nx, ny, 0.6, 0.05, seed=nx + ny)
+        compare(c, 25)
+
+
+def test_obstacle_channel_with_uniform_force():
+    c = wl.channel_obstacle(nx=260, ny=48, D=8, Re=20.0, U0=0.05, gamma=0.3, xc=60)
+    dpop, du, (rg, ug, vg), _ = compare(c, 200)
+    assert np.all(np.isnan(ug[c.solid == 1]))
+
+
+def test_variable_force_field():
+    c = wl.four_rolls_mill(64, 0.045, 20.0, 0.3)
+    compare(c, 150)
+
+
+def test_fp64_storage_matches_tightly():
+    c = wl.random_cavity_state(150, 33, 0.4, Re=60.0, seed=2)
+    compare(c, 80, storage=lbm.STORAGE_F64, pop_tol=1e-12)
+
+
+@pytest.mark.parametrize("storage,tol", [(lbm.STORAGE_F16, 2e-4), (lbm.STORAGE_BF16, 2e-3)])
+def test_reduced_precision_storage(storage, tol):
+    """FP16/BF16 deviations with FP32 collision: velocity error bound relative to U
+    after 200 steps of a cavity (rounding of the stored deviations)."""
+    c = wl.cavity(96, 100.0, 0.1, 0.5)
+    g = lbm.solver_from_case(c, storage=storage)
+    o = oracle_for(c)
+    g.step(200)
+    o.step(200)
+    _, ug, vg = g.fields()
+    _, uo, vo = o.fields()
+    err = max(np.abs(ug - uo).max(), np.abs(vg - vo).max()) / c.U
+    assert err < tol, err
+
+
+def test_residual_and_sums_match_oracle():
+    c = wl.random_cavity_state(140, 50, 0.5, Re=50.0, seed=9)
+    g = lbm.solver_from_case(c)
+    o = oracle_for(c)
+    for n in (10, 30):
+        g.step(n)
+        o.step(n)
+        rg, sg = g.residual()
+        ro, so = o.residual()
+        assert abs(rg - ro) <= 1e-5 * ro
+        assert np.allclose(sg, so, rtol=1e-6, atol=1e-9)
+
+
+def test_mass_conserved_in_cavity():
+    c = wl.random_cavity_state(257, 130, 0.5, Re=100.0, seed=1)
+    g = lbm.solver_from_case(c)
+    _, s0 = g.residual()
+    g.step(500)
+    _, s1 = g.residual()
+    assert abs(s1[2] - s0[2]) / s0[2] < 1e-6
+
+
+def test_checkpoint_resume_bit_exact(tmp_path):
+    c = wl.random_cavity_state(130, 40, 0.5, Re=50.0, seed=3)
+    a = lbm.solver_from_case(c)
+    a.step(70)
+    fa = a.populations()
+    b = lbm.solver_from_case(c)
+    b.step(30)
+    b.save(tmp_path / "ck.bin")
+    b2 = lbm.solver_from_case(c)
+    b2.load(tmp_path / "ck.bin")
+    assert b2.steps == 30
+    b2.step(40)
+    assert np.array_equal(b2.populations(), fa)
+
+
+def test_run_to_steady_small_cavity_matches_oracle_steady_state():
+    """Steady state of a 24 x 24 cavity (Re = 20, gamma = 0.5): relative L2 of u
+    between GPU FP32 and oracle FP64 <= 1e-6."""
+    c = wl.cavity(24, 20.0, 0.1, 0.5)
+    g = lbm.solver_from_case(c)
+    st, steps, r = g.run_to_steady(1e-10, 500, 200000)
+    assert st == 0 and r < 1e-10
+    o = oracle_for(c)
+    for _ in range(400):
+        o.step(500)
+        ro, _ = o.residual()
+        if ro < 1e-12:
+            break
+    _, ug, vg = g.fields()
+    _, uo, vo = o.fields()
+    l2 = np.sqrt(((ug - uo) ** 2 + (vg - vo) ** 2).sum() / (uo**2 + vo**2).sum())
+    assert l2 <= 1e-6, l2
+
+
+def test_diverged_run_reports_status():
+    """A state with a NaN (planted on the host through the API) is reported as
+    LBM_ERR_DIVERGED, not as convergence."""
+    c = wl.cavity(32, 100.0, 0.1, 0.5)
+    g = lbm.solver_from_case(c)
+    f = g.populations()
+    f[0, 5, 5] = np.nan
+    g.set_populations(f)
+    st, steps, r = g.run_to_steady(1e-8, 10, 100, raise_on_error=False)
+    assert st == lbm.ERR_DIVERGED
+
+
+def _window_check(fg_prev, fg_next, case, x0, y0, w, h, gi_mode=orc.GI_FULL):
+    """Advance the window [x0-2, x0+w+2) x [y0-2, y0+h+2) of the GPU state at
+    step n-1 with the oracle and compare the interior with the GPU's step n.
+    Sides of the window that coincide with the domain's sides keep the domain's
+    boundary; the others only affect the discarded margin."""
+    nx, ny = case.nx, case.ny
+    xa, xb = max(x0 - 2, 0), min(x0 + w + 2, nx)
+    ya, yb = max(y0 - 2, 0), min(y0 + h + 2, ny)
+    sides = [list(s) for s in case.sides]
+    fake = (wl.WALL, 0.0, 0.0)
+    west = case.sides[0] if xa == 0 else fake
+    east = case.sides[1] if xb == nx else fake
+    south = case.sides[2] if ya == 0 else fake
+    north = case.sides[3] if yb == ny else fake
+    win = orc.Domain(xb - xa, yb - ya, case.nu, case.gamma, (west, east, south, north), gi_mode=gi_mode)
+    win.set_pops(fg_prev[:, ya:yb, xa:xb])
+    win.step(1)
+    fo = win.pops()
+    ix = slice(x0 - xa, x0 - xa + w)
+    iy = slice(y0 - ya, y0 - ya + h)
+    ref = fo[:, iy, ix]
+    got = fg_next[:, y0:y0 + h, x0:x0 + w]
+    return np.abs(ref - got).max()
+
+
+def test_full_size_4096_cavity_sampled_windows():
+    """The bench workload (4096 x 4096 cavity, Re = 1000, gamma = 0.5) in the
+    bench's launch configuration: after 300 steps, sampled windows at the four
+    corners, the lid, the walls, strip/segment seams and the interior agree with
+    one oracle step taken from the GPU's previous state."""
+    c = wl.cavity(4096, 1000.0, 0.1, 0.5)
+    g = lbm.solver_from_case(c)
+    g.step(299)
+    fprev = g.populations()
+    g.step(1)
+    fnext = g.populations()
+    n = 4096
+    windows = [(0, 0), (n - 12, 0), (0, n - 12), (n - 12, n - 12), (2040, n - 12), (0, 2000),
+               (n - 12, 3000), (1500, 0), (120, 50), (250, 1777), (2047, 2047), (127, 53)]
+    worst = 0.0
+    for (x0, y0) in windows:
+        worst = max(worst, _window_check(fprev, fnext, c, x0, y0, 12, 12))
+    assert worst < 2e-6, worst
+    # mass is conserved over the whole run
+    _, ug, _ = g.fields()
+    assert np.isfinite(ug).all()
