@@ -11,13 +11,6 @@
 
 #include "lbm_internal.h"
 
-namespace lbm {
-int blocks_per_sm_f32(int gi_mode);
-int blocks_per_sm_f16(int gi_mode);
-int blocks_per_sm_bf16(int gi_mode);
-int blocks_per_sm_f64(int gi_mode);
-}  // namespace lbm
-
 using namespace lbm;
 
 namespace {
@@ -90,6 +83,8 @@ struct lbm_ctx {
     float *d_force = nullptr;
     double *d_snap_ux = nullptr, *d_snap_uy = nullptr, *d_partials = nullptr, *d_result = nullptr;
     unsigned long long *d_guard = nullptr;
+    int *d_err = nullptr;        // set by a step kernel whose bounded wait expired
+    CUtensorMap tmap[2];         // TMA descriptors of f[0], f[1]
     double *h_result = nullptr;  // pinned, 5 doubles
     int res_blocks = 1;
     cudaStream_t own_stream = nullptr, stream = nullptr;
@@ -130,6 +125,7 @@ StepParams make_params(const lbm_ctx *c)
     p.force = c->d_force;
     p.solid = c->d_solid;
     p.guard_count = c->d_guard;
+    p.error = c->d_err;
     p.nstrips = (c->nx + BW - 1) / BW;
     int bps = 1;
     switch (c->storage) {
@@ -141,8 +137,9 @@ StepParams make_params(const lbm_ctx *c)
     const int resident = c->num_sms * bps;
     int Ly = c->Ly_option;
     if (Ly <= 0) {
-        // about four items per resident block, segments of at least 2 rows
-        const int nseg = (4 * resident + p.nstrips - 1) / p.nstrips;
+        // one item per resident block: long segments keep the four halo source
+        // rows of each segment a small fraction of the traffic
+        const int nseg = (resident + p.nstrips - 1) / p.nstrips;
         Ly = (c->ny + nseg - 1) / nseg;
         if (Ly < 2) Ly = 2;
     }
@@ -166,14 +163,39 @@ int step_grid(const lbm_ctx *c, const StepParams &p)
     return p.nitems < resident ? p.nitems : resident;
 }
 
-cudaError_t launch_step(const lbm_ctx *c, const StepParams &p, int grid, const void *fin, void *fout)
+cudaError_t launch_step(const lbm_ctx *c, const StepParams &p, int grid)
 {
+    const CUtensorMap &tin = c->tmap[c->cur];
+    const void *fin = c->f[c->cur];
+    void *fout = c->f[1 - c->cur];
     switch (c->storage) {
-    case LBM_STORAGE_F16: return launch_step_f16(p, fin, fout, grid, c->stream);
-    case LBM_STORAGE_BF16: return launch_step_bf16(p, fin, fout, grid, c->stream);
-    case LBM_STORAGE_F64: return launch_step_f64(p, fin, fout, grid, c->stream);
-    default: return launch_step_f32(p, fin, fout, grid, c->stream);
+    case LBM_STORAGE_F16: return launch_step_f16(p, tin, fin, fout, grid, c->stream);
+    case LBM_STORAGE_BF16: return launch_step_bf16(p, tin, fin, fout, grid, c->stream);
+    case LBM_STORAGE_F64: return launch_step_f64(p, tin, fin, fout, grid, c->stream);
+    default: return launch_step_f32(p, tin, fin, fout, grid, c->stream);
     }
+}
+
+cudaError_t build_tensor_maps(lbm_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = make_tensor_map(&c->tmap[k], c->storage, c->f[k], c->nx, c->ny, c->pitch, c->plane);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// A step kernel that gave up on a bounded wait leaves a flag; report it once.
+lbm_status check_device_error(lbm_ctx *c)
+{
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error flag");
+    if (v) {
+        cudaMemset(c->d_err, 0, sizeof(int));
+        return fail(LBM_ERR_CUDA, "a step kernel's bounded wait for its staged rows expired");
+    }
+    return LBM_OK;
 }
 
 bool valid_omega(double w) { return w > 0.0 && w < 2.0 && isfinite(w); }
@@ -198,6 +220,7 @@ void free_ctx(lbm_ctx *c)
     dev_free(c->d_partials);
     dev_free(c->d_result);
     dev_free(c->d_guard);
+    dev_free(c->d_err);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -289,7 +312,9 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const l
     c->d_partials = (double *)dev_alloc((size_t)c->res_blocks * 5 * sizeof(double));
     c->d_result = (double *)dev_alloc(8 * sizeof(double));
     c->d_guard = (unsigned long long *)dev_alloc(sizeof(unsigned long long));
-    if (!c->f[0] || !c->f[1] || !c->d_snap_ux || !c->d_snap_uy || !c->d_partials || !c->d_result || !c->d_guard) {
+    c->d_err = (int *)dev_alloc(sizeof(int));
+    if (!c->f[0] || !c->f[1] || !c->d_snap_ux || !c->d_snap_uy || !c->d_partials || !c->d_result || !c->d_guard ||
+        !c->d_err) {
         free_ctx(c);
         return fail(LBM_ERR_OOM, "device allocation failed");
     }
@@ -313,7 +338,13 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const l
             return cuda_fail(e, "cudaMemcpy(mask)");
         }
     }
+    e = build_tensor_maps(c);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return cuda_fail(e, "cuTensorMapEncodeTiled");
+    }
     e = cudaMemsetAsync(c->d_guard, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, pop_bytes(c), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_snap_ux, 0, N * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_snap_uy, 0, N * sizeof(double), c->stream);
@@ -397,6 +428,8 @@ lbm_status lbm_set_option(lbm_ctx *c, const char *key, double v)
         c->f[0] = nf0;
         c->f[1] = nf1;
         c->cur = 0;
+        e = build_tensor_maps(c);
+        if (e != cudaSuccess) return cuda_fail(e, "cuTensorMapEncodeTiled");
     } else {
         return fail(LBM_ERR_INVALID, "unknown option: " + k);
     }
@@ -482,7 +515,7 @@ lbm_status lbm_step(lbm_ctx *c, long n)
     StepParams p = make_params(c);
     const int grid = step_grid(c, p);
     for (long i = 0; i < n; ++i) {
-        cudaError_t e = launch_step(c, p, grid, c->f[c->cur], c->f[1 - c->cur]);
+        cudaError_t e = launch_step(c, p, grid);
         if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
         c->cur = 1 - c->cur;
         c->steps += 1;
@@ -498,6 +531,8 @@ lbm_status lbm_residual(lbm_ctx *c, double *residual, double sums[5])
     if (s != LBM_OK) return s;
     LBM_CUDA(cudaMemcpyAsync(c->h_result, c->d_result, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
+    s = check_device_error(c);
+    if (s != LBM_OK) return s;
     const double du2 = c->h_result[0], u2 = c->h_result[1];
     double r;
     if (!isfinite(du2) || !isfinite(u2)) r = NAN;
@@ -562,6 +597,8 @@ lbm_status lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy)
     StepParams p = make_params(c);
     LBM_CUDA(launch_fields(p, c->storage, c->f[c->cur], d, d + N, d + 2 * N, c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
+    lbm_status s = check_device_error(c);
+    if (s != LBM_OK) return s;
     if (rho) LBM_CUDA(cudaMemcpy(rho, d, N * 8, cudaMemcpyDeviceToHost));
     if (ux) LBM_CUDA(cudaMemcpy(ux, d + N, N * 8, cudaMemcpyDeviceToHost));
     if (uy) LBM_CUDA(cudaMemcpy(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost));
@@ -578,6 +615,8 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
     StepParams p = make_params(c);
     LBM_CUDA(launch_pops_to_f64(p, c->storage, c->f[c->cur], (double *)b.p, c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
+    lbm_status s = check_device_error(c);
+    if (s != LBM_OK) return s;
     LBM_CUDA(cudaMemcpy(f, b.p, 9 * N * 8, cudaMemcpyDeviceToHost));
     return LBM_OK;
 }

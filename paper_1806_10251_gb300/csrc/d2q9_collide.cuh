@@ -32,21 +32,25 @@ template <typename ST> struct StorageTraits;
 template <> struct StorageTraits<float> {
     using R = float;
     __device__ static __forceinline__ float load(const float *p) { return __ldg(p); }
+    __device__ static __forceinline__ float cvt(float v) { return v; }
     __device__ static __forceinline__ void store(float *p, float v) { *p = v; }
 };
 template <> struct StorageTraits<double> {
     using R = double;
     __device__ static __forceinline__ double load(const double *p) { return __ldg(p); }
+    __device__ static __forceinline__ double cvt(double v) { return v; }
     __device__ static __forceinline__ void store(double *p, double v) { *p = v; }
 };
 template <> struct StorageTraits<__half> {
     using R = float;
     __device__ static __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ float cvt(__half v) { return __half2float(v); }
     __device__ static __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct StorageTraits<__nv_bfloat16> {
     using R = float;
     __device__ static __forceinline__ float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 

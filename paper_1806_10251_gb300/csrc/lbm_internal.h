@@ -1,6 +1,7 @@
 // Internal types shared by the translation units of the CUDA library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,16 +33,23 @@ struct StepParams {
     const float *force;      // optional per-cell force: [2][ny][pitch] (fx, fy)
     const uint8_t *solid;    // optional mask [ny][pitch], 1 = solid
     unsigned long long *guard_count;  // device counter, may be null
+    int *error;              // device flag: set when a bounded wait expires
     // work decomposition: items = strips x segments, each segment Ly rows
     int Ly, nstrips, nitems;
 };
 
 // The launchers below are defined per storage type (one translation unit each).
-cudaError_t launch_step_f32(const StepParams &p, const void *fin, void *fout, int grid, cudaStream_t s);
-cudaError_t launch_step_f16(const StepParams &p, const void *fin, void *fout, int grid, cudaStream_t s);
-cudaError_t launch_step_bf16(const StepParams &p, const void *fin, void *fout, int grid, cudaStream_t s);
-cudaError_t launch_step_f64(const StepParams &p, const void *fin, void *fout, int grid, cudaStream_t s);
-int step_blocks_per_sm(int storage, int gi_mode, bool solid);
+// tin is the TMA descriptor of fin (3-D: x, y, population plane).
+cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid, cudaStream_t s);
+cudaError_t launch_step_f16(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid, cudaStream_t s);
+cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid, cudaStream_t s);
+cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid, cudaStream_t s);
+int blocks_per_sm_f32(int gi_mode);
+int blocks_per_sm_f16(int gi_mode);
+int blocks_per_sm_bf16(int gi_mode);
+int blocks_per_sm_f64(int gi_mode);
+// Encode the TMA descriptor of a population buffer (box: one row of all planes).
+cudaError_t make_tensor_map(CUtensorMap *map, int storage, void *base, int nx, int ny, int pitch, long long plane);
 
 // Auxiliary kernels (aux_kernels.cu)
 cudaError_t launch_init_eq(const StepParams &p, int storage, const double *rho, const double *ux,

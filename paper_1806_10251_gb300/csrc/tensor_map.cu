@@ -1,0 +1,56 @@
+// TMA descriptors of the population buffers: a 3-D tensor (x, y, plane) whose
+// box is one row of all nine planes plus the halo columns of a strip.
+#include <cudaTypedefs.h>
+
+#include "stream_collide.cuh"
+
+namespace lbm {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+template <typename ST>
+cudaError_t encode(CUtensorMap *map, CUtensorMapDataType dtype, void *base, int nx, int ny, int pitch,
+                   long long plane)
+{
+    using T = Tile<ST>;
+    auto fn = encoder();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(ST), (cuuint64_t)plane * sizeof(ST)};
+    const cuuint32_t box[3] = {(cuuint32_t)T::BWX, 1, 9};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, dtype, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t make_tensor_map(CUtensorMap *map, int storage, void *base, int nx, int ny, int pitch, long long plane)
+{
+    switch (storage) {
+    case LBM_STORAGE_F16: return encode<__half>(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, base, nx, ny, pitch, plane);
+    case LBM_STORAGE_BF16:
+        return encode<__nv_bfloat16>(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, nx, ny, pitch, plane);
+    case LBM_STORAGE_F64: return encode<double>(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, base, nx, ny, pitch, plane);
+    default: return encode<float>(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, base, nx, ny, pitch, plane);
+    }
+}
+
+}  // namespace lbm
