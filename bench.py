@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--gi-mode", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-check-every", type=int, default=100)
+    ap.add_argument("--cells-per-item", type=int, default=0,
+                    help="rows per work item of the step kernel (0 = automatic)")
     return ap.parse_args()
 
 
@@ -220,6 +222,8 @@ def main():
     g.set_option("gi_mode", args.gi_mode)
     if args.storage != "f32":
         g.set_option("storage", STORAGE_CODE[args.storage])
+    if args.cells_per_item:
+        g.set_option("cells_per_item", args.cells_per_item)
     # A dedicated stream: its handle is non-zero, so the library launches on it
     # and the CUDA events below time exactly those launches.
     stream = torch.cuda.Stream()
@@ -279,6 +283,8 @@ def main():
     g2.set_option("gi_mode", args.gi_mode)
     if args.storage != "f32":
         g2.set_option("storage", STORAGE_CODE[args.storage])
+    if args.cells_per_item:
+        g2.set_option("cells_per_item", args.cells_per_item)
     g2.set_stream(stream.cuda_stream)
     g2.init_fields(rho0, ux0, uy0)
     g2.step(args.warmup)
@@ -312,6 +318,8 @@ def main():
             "config": {"workload": f"lid-driven cavity {args.n}x{args.n}, U=0.1, Re={args.Re:g}, "
                                    f"gamma={args.gamma:g}, GI mode {args.gi_mode}, from rest",
                        "storage": args.storage, "replicas": world,
+                       "rows_per_item": int(g.get_option("cells_per_item")),
+                       "grid": int(g.get_option("grid")),
                        "l2": "no flush: populations (per replica) exceed the 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,

@@ -581,7 +581,11 @@ lbm_status lbm_run_to_steady(lbm_ctx *c, double tol, long check_every, long max_
             }
         }
     }
-    if (st == LBM_ERR_NOT_CONVERGED) fail(st, "max_steps reached with residual " + std::to_string(r));
+    if (st == LBM_ERR_NOT_CONVERGED) {
+        char buf[64];
+        snprintf(buf, sizeof(buf), "%.3e", r);
+        fail(st, std::string("max_steps reached with residual ") + buf);
+    }
     if (steps_done) *steps_done = done;
     if (final_residual) *final_residual = r;
     return st;

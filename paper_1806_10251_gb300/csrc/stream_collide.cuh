@@ -139,7 +139,8 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
         const int x = x0 + tid;
         const int col = tid + T::PAD;             // smem column of this thread's cell
         const bool fix_left = p.perx && x0 == 0;
-        const bool fix_right = p.perx && x0 + BW >= p.nx;
+        // the box reaches column nx (right halo x0 + BW pulls from x0 + BW + 1)
+        const bool fix_right = p.perx && x0 + BW + 1 >= p.nx;
         const bool fast_x = !has_solid && (p.perx || (x0 >= 2 && x0 + BW + 2 <= p.nx));
 
         auto slot_of = [&](int k) -> int { return (int)((q_base + (uint32_t)k) % T::NSLOT); };
@@ -176,9 +177,11 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                     // left: columns -2, -1 <- nx-2, nx-1; right: nx, nx+1 <- 0, 1
                     const int xd = side == 0 ? j - 2 : p.nx + j;
                     const int xs = side == 0 ? p.nx - 2 + j : j;
-                    ST *dst = reinterpret_cast<ST *>(smem + slot * T::SLOT_BYTES);
-                    dst[a * T::BWX + (xd - x0 + T::PAD)] =
-                        fin[(size_t)a * (size_t)p.plane + (size_t)s * p.pitch + xs];
+                    const int cd = xd - x0 + T::PAD;
+                    if (cd >= 0 && cd < T::BWX) {
+                        ST *dst = reinterpret_cast<ST *>(smem + slot * T::SLOT_BYTES);
+                        dst[a * T::BWX + cd] = fin[(size_t)a * (size_t)p.plane + (size_t)s * p.pitch + xs];
+                    }
                 }
             }
         };

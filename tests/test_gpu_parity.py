@@ -163,8 +163,8 @@ def test_run_to_steady_small_cavity_matches_oracle_steady_state():
     GPU FP32 and the oracle's FP64 steady state (r < 1e-12) <= 1e-6."""
     c = wl.cavity(24, 20.0, 0.1, 0.5)
     g = lbm.solver_from_case(c)
-    st, steps, r = g.run_to_steady(1e-8, 1000, 400000)
-    print("GPU steady: steps", steps, "residual", r)
+    st, steps, r = g.run_to_steady(1e-8, 1000, 400000, raise_on_error=False)
+    print("GPU steady: status", st, "steps", steps, "residual", r)
     assert st == 0 and r < 1e-8
     o = oracle_for(c)
     for _ in range(400):
@@ -249,7 +249,8 @@ def test_cavity_128_steady_state_against_oracle_golden():
     c = wl.cavity(128, 100.0, 0.1, 0.5)
     g = lbm.solver_from_case(c)
     g.step(4000)
-    st, steps, r = g.run_to_steady(1e-8, 1000, 400000)
+    st, steps, r = g.run_to_steady(1e-8, 1000, 400000, raise_on_error=False)
+    print("128^2 GPU steady: status", st, "steps", steps, "residual", r)
     assert st == 0 and r < 1e-8
     _, ug, vg = g.fields()
     uo, vo = gold["ux"].astype(np.float64), gold["uy"].astype(np.float64)
