@@ -84,7 +84,8 @@ struct lbm_ctx {
     double *d_snap_ux = nullptr, *d_snap_uy = nullptr, *d_partials = nullptr, *d_result = nullptr;
     unsigned long long *d_guard = nullptr;
     int *d_err = nullptr;        // set by a step kernel whose bounded wait expired
-    CUtensorMap tmap[2];         // TMA descriptors of f[0], f[1]
+    CUtensorMap tload[2];        // TMA load descriptors of f[0], f[1]
+    CUtensorMap tstore[2];       // TMA store descriptors of f[0], f[1]
     double *h_result = nullptr;  // pinned, 5 doubles
     int res_blocks = 1;
     cudaStream_t own_stream = nullptr, stream = nullptr;
@@ -126,7 +127,9 @@ StepParams make_params(const lbm_ctx *c)
     p.solid = c->d_solid;
     p.guard_count = c->d_guard;
     p.error = c->d_err;
-    p.nstrips = (c->nx + BW - 1) / BW;
+    p.cf.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
+    p.cd.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
+    p.nstrips = (c->nx + WS - 1) / WS;
     int bps = 1;
     switch (c->storage) {
     case LBM_STORAGE_F16: bps = blocks_per_sm_f16(c->gi_mode); break;
@@ -134,12 +137,13 @@ StepParams make_params(const lbm_ctx *c)
     case LBM_STORAGE_F64: bps = blocks_per_sm_f64(c->gi_mode); break;
     default: bps = blocks_per_sm_f32(c->gi_mode); break;
     }
-    const int resident = c->num_sms * bps;
+    const int resident = c->num_sms * bps * WARPS;  // resident warps
     int Ly = c->Ly_option;
     if (Ly <= 0) {
-        // one item per resident block: long segments keep the four halo source
-        // rows of each segment a small fraction of the traffic
-        const int nseg = (resident + p.nstrips - 1) / p.nstrips;
+        // at most one item per resident warp (no partly filled second round);
+        // long segments keep the four halo source rows of each a small fraction
+        int nseg = resident / p.nstrips;
+        if (nseg < 1) nseg = 1;
         Ly = (c->ny + nseg - 1) / nseg;
         if (Ly < 2) Ly = 2;
     }
@@ -160,26 +164,28 @@ int step_grid(const lbm_ctx *c, const StepParams &p)
     default: bps = blocks_per_sm_f32(c->gi_mode); break;
     }
     const int resident = c->num_sms * bps;
-    return p.nitems < resident ? p.nitems : resident;
+    const int blocks = (p.nitems + WARPS - 1) / WARPS;
+    return blocks < resident ? blocks : resident;
 }
 
 cudaError_t launch_step(const lbm_ctx *c, const StepParams &p, int grid)
 {
-    const CUtensorMap &tin = c->tmap[c->cur];
+    const CUtensorMap &tin = c->tload[c->cur];
+    const CUtensorMap &tout = c->tstore[1 - c->cur];
     const void *fin = c->f[c->cur];
-    void *fout = c->f[1 - c->cur];
     switch (c->storage) {
-    case LBM_STORAGE_F16: return launch_step_f16(p, tin, fin, fout, grid, c->stream);
-    case LBM_STORAGE_BF16: return launch_step_bf16(p, tin, fin, fout, grid, c->stream);
-    case LBM_STORAGE_F64: return launch_step_f64(p, tin, fin, fout, grid, c->stream);
-    default: return launch_step_f32(p, tin, fin, fout, grid, c->stream);
+    case LBM_STORAGE_F16: return launch_step_f16(p, tin, tout, fin, grid, c->stream);
+    case LBM_STORAGE_BF16: return launch_step_bf16(p, tin, tout, fin, grid, c->stream);
+    case LBM_STORAGE_F64: return launch_step_f64(p, tin, tout, fin, grid, c->stream);
+    default: return launch_step_f32(p, tin, tout, fin, grid, c->stream);
     }
 }
 
 cudaError_t build_tensor_maps(lbm_ctx *c)
 {
     for (int k = 0; k < 2; ++k) {
-        cudaError_t e = make_tensor_map(&c->tmap[k], c->storage, c->f[k], c->nx, c->ny, c->pitch, c->plane);
+        cudaError_t e =
+            make_tensor_maps(&c->tload[k], &c->tstore[k], c->storage, c->f[k], c->nx, c->ny, c->pitch, c->plane);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

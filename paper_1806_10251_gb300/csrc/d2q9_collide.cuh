@@ -54,41 +54,6 @@ template <> struct StorageTraits<__nv_bfloat16> {
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
-// ---- per-launch constants in the compute precision ---------------------------
-template <typename R>
-struct Consts {
-    R ig, half_ig;                 // 1/gamma, 1/(2 gamma)
-    R ig2;                         // 1/gamma^2
-    R w3_12, w4_4, w5_4, w6_4, w7_4, w8_4;
-    R c6;                          // third-order factor: 2 (Eq. 4) or 3/g - 1/g^2 (Sec. 5)
-    R A, B, C3;                    // A_gamma, B_gamma, C_gamma/3 (after Eq. 53)
-    R k3, k4, k5;                  // 1/omega_j - 1/2
-    R a3, a4;                      // 2/(3 omega3), 2/(3 omega4)
-
-    __device__ __forceinline__ void init(const StepParams &p)
-    {
-        const double g = p.gamma;
-        ig = R(1.0 / g);
-        half_ig = R(0.5 / g);
-        ig2 = R(1.0 / (g * g));
-        w3_12 = R(p.w3 / 12.0);
-        w4_4 = R(p.w4 / 4.0);
-        w5_4 = R(p.w5 / 4.0);
-        w6_4 = R(p.w6 / 4.0);
-        w7_4 = R(p.w7 / 4.0);
-        w8_4 = R(p.w8 / 4.0);
-        c6 = p.gi_mode == LBM_GI_UNCORRECTED ? R(2.0) : R(3.0 / g - 1.0 / (g * g));
-        A = R(4.0 / (g * g) - 1.0 / g);
-        B = R(1.0 / (g * g) - 1.0 / g);
-        C3 = R((1.0 / g - 1.0) / 3.0);
-        k3 = R(1.0 / p.w3 - 0.5);
-        k4 = R(1.0 / p.w4 - 0.5);
-        k5 = R(1.0 / p.w5 - 0.5);
-        a3 = R(2.0 / (3.0 * p.w3));
-        a4 = R(2.0 / (3.0 * p.w4));
-    }
-};
-
 // One cell: g holds the post-streaming deviations gbar on entry and the
 // post-collision deviations on exit (Eq. 2a: f~ = fbar + K g^ + S).
 // drx, dry: density gradient (used by the full kernel only).

@@ -11,11 +11,53 @@
 
 namespace lbm {
 
-// Threads per block of the stream-collide kernel: one strip of BW columns.
-constexpr int BW = 128;
+// Columns of one warp strip of the stream-collide kernel, warps per block.
+constexpr int WS = 32;
+constexpr int WARPS = 4;
+constexpr int BW = WS * WARPS;  // threads per block
+
+// Collision constants in the compute precision, filled on the host once per
+// launch (no FP64 arithmetic in the FP32 kernels).
+template <typename R>
+struct Consts {
+    R ig, half_ig;                 // 1/gamma, 1/(2 gamma)
+    R ig2;                         // 1/gamma^2
+    R w3_12, w4_4, w5_4, w6_4, w7_4, w8_4;
+    R c6;                          // third-order factor: 2 (Eq. 4) or 3/g - 1/g^2 (Sec. 5)
+    R A, B, C3;                    // A_gamma, B_gamma, C_gamma/3 (after Eq. 53)
+    R k3, k4, k5;                  // 1/omega_j - 1/2
+    R a3, a4;                      // 2/(3 omega3), 2/(3 omega4)
+    R Fx, Fy;                      // uniform force
+    R wall6[4][2];                 // 6 u_wall of each side (west, east, south, north)
+
+    void set(double g, const double w[9], int gi_mode, double fx, double fy, const double side_u[4][2])
+    {
+        ig = R(1.0 / g);
+        half_ig = R(0.5 / g);
+        ig2 = R(1.0 / (g * g));
+        w3_12 = R(w[3] / 12.0);
+        w4_4 = R(w[4] / 4.0);
+        w5_4 = R(w[5] / 4.0);
+        w6_4 = R(w[6] / 4.0);
+        w7_4 = R(w[7] / 4.0);
+        w8_4 = R(w[8] / 4.0);
+        c6 = gi_mode == LBM_GI_UNCORRECTED ? R(2.0) : R(3.0 / g - 1.0 / (g * g));
+        A = R(4.0 / (g * g) - 1.0 / g);
+        B = R(1.0 / (g * g) - 1.0 / g);
+        C3 = R((1.0 / g - 1.0) / 3.0);
+        k3 = R(1.0 / w[3] - 0.5);
+        k4 = R(1.0 / w[4] - 0.5);
+        k5 = R(1.0 / w[5] - 0.5);
+        a3 = R(2.0 / (3.0 * w[3]));
+        a4 = R(2.0 / (3.0 * w[4]));
+        Fx = R(fx);
+        Fy = R(fy);
+        for (int s = 0; s < 4; ++s)
+            for (int d = 0; d < 2; ++d) wall6[s][d] = R(6.0 * side_u[s][d]);
+    }
+};
 
 // Everything one launch of the step kernel needs, passed by value.
-// Physical parameters are kept in double and converted once per thread.
 struct StepParams {
     int nx, ny;
     int pitch;              // row stride in elements (multiple of 32)
@@ -34,22 +76,27 @@ struct StepParams {
     const uint8_t *solid;    // optional mask [ny][pitch], 1 = solid
     unsigned long long *guard_count;  // device counter, may be null
     int *error;              // device flag: set when a bounded wait expires
-    // work decomposition: items = strips x segments, each segment Ly rows
+    // work decomposition: items = warp strips x segments, each segment Ly rows
     int Ly, nstrips, nitems;
+    Consts<float> cf;
+    Consts<double> cd;
 };
 
 // The launchers below are defined per storage type (one translation unit each).
-// tin is the TMA descriptor of fin (3-D: x, y, population plane).
-cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid, cudaStream_t s);
-cudaError_t launch_step_f16(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid, cudaStream_t s);
-cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid, cudaStream_t s);
-cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid, cudaStream_t s);
+// tin: TMA descriptor of fin for loads (box: one row of all planes of a warp
+// strip plus halo); tout: descriptor of fout for stores (box: one strip row).
+cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
+cudaError_t launch_step_f16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
+cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
+cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
 int blocks_per_sm_f32(int gi_mode);
 int blocks_per_sm_f16(int gi_mode);
 int blocks_per_sm_bf16(int gi_mode);
 int blocks_per_sm_f64(int gi_mode);
-// Encode the TMA descriptor of a population buffer (box: one row of all planes).
-cudaError_t make_tensor_map(CUtensorMap *map, int storage, void *base, int nx, int ny, int pitch, long long plane);
+// Encode the TMA descriptors of a population buffer: load box {WS + 2 PAD, 1, 9}
+// and store box {WS, 1, 9}.
+cudaError_t make_tensor_maps(CUtensorMap *load, CUtensorMap *store, int storage, void *base, int nx, int ny,
+                             int pitch, long long plane);
 
 // Auxiliary kernels (aux_kernels.cu)
 cudaError_t launch_init_eq(const StepParams &p, int storage, const double *rho, const double *ux,

@@ -3,10 +3,10 @@
 
 namespace lbm {
 
-cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid,
-                           cudaStream_t s)
+cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin,
+                           int grid, cudaStream_t s)
 {
-    return launch_step_t<__nv_bfloat16>(p, tin, fin, fout, grid, s);
+    return launch_step_t<__nv_bfloat16>(p, tin, tout, fin, grid, s);
 }
 
 int blocks_per_sm_bf16(int gi_mode) { return blocks_per_sm_t<__nv_bfloat16>(gi_mode); }

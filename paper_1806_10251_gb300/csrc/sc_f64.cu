@@ -3,10 +3,10 @@
 
 namespace lbm {
 
-cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid,
-                           cudaStream_t s)
+cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin,
+                           int grid, cudaStream_t s)
 {
-    return launch_step_t<double>(p, tin, fin, fout, grid, s);
+    return launch_step_t<double>(p, tin, tout, fin, grid, s);
 }
 
 int blocks_per_sm_f64(int gi_mode) { return blocks_per_sm_t<double>(gi_mode); }
