@@ -54,14 +54,20 @@ template <> struct StorageTraits<__nv_bfloat16> {
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Reciprocal: correctly rounded in FP32 (no IEEE division sequence), exact
+// division in FP64.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // One cell: g holds the post-streaming deviations gbar on entry and the
 // post-collision deviations on exit (Eq. 2a: f~ = fbar + K g^ + S).
-// drx, dry: density gradient (used by the full kernel only).
-template <typename R, int MODE>
-__device__ __forceinline__ void collide_cell(R (&g)[9], R drx, R dry, R Fx, R Fy, bool forced,
-                                             const Consts<R> &c, bool guard,
-                                             unsigned long long *guard_count)
+// drx, dry: density gradient (used by the full kernel only).  FORCED selects
+// the variant with the preconditioned source terms.
+template <typename R, int MODE, bool FORCED>
+__device__ __forceinline__ void collide_cell(R (&g)[9], R drx, R dry, R Fx, R Fy, const Consts<R> &c,
+                                             bool guard, unsigned long long *guard_count)
 {
+    constexpr bool forced = FORCED;
     const R third = R(1.0 / 3.0);
     // conserved moments (Eq. 3 on gbar; rho = 1 + sum g)
     const R kxxyy = (g[5] + g[6]) + (g[7] + g[8]);
@@ -69,7 +75,7 @@ __device__ __forceinline__ void collide_cell(R (&g)[9], R drx, R dry, R Fx, R Fy
     const R kyy = (g[2] + g[4]) + kxxyy;
     const R dr = g[0] + (g[1] + g[3]) + (g[2] + g[4]) + kxxyy;
     const R rho = R(1) + dr;
-    const R irho = R(1) / rho;
+    const R irho = recip(rho);
     const R jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
     const R jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
     // velocity with the forcing shift: rho u = sum fbar e + F/(2 gamma)
@@ -121,7 +127,7 @@ __device__ __forceinline__ void collide_cell(R (&g)[9], R drx, R dry, R Fx, R Fy
         const R er = c.C3 * (ux * drx + uy * dry);
         const R ert = c.C3 * (ux * drx - uy * dry);
         const R R3 = m3 - er, R4 = m4 - ert;
-        const R iD = R(1) / D;
+        const R iD = recip(D);
         // Eq. 55a, and 55b with the c~1 term's sign as the solve of Eqs. 51-52 gives it
         const R dux = (c2t * R3 + c2 * R4) * iD;
         const R duy = (c1t * R3 - c1 * R4) * iD;

@@ -18,7 +18,11 @@
 // the cell's own density for that neighbour (one-sided half difference).
 //
 // Stores: each lane writes its nine post-collision values into the warp's
-// double-buffered stage; one TMA bulk-tensor store per row writes them to HBM.
+// stage buffer; one TMA bulk-tensor store per row writes them to HBM.
+//
+// Rows whose pulls meet no wall, solid or ragged edge take a path without any
+// boundary logic (and the strip's halo densities come from one shared-memory
+// load per lane and a 16-lane shuffle sum); the general path handles the rest.
 //
 // Periodic sides: source rows wrap when the copy is issued (y); the two halo
 // columns beyond a periodic x edge are patched from global memory when a row
@@ -46,7 +50,7 @@ struct Tile {
     static constexpr int NSLOT = 8;                   // power of two
     static constexpr int STAGE_BYTES = (9 * WS * ES + 127) / 128 * 128;
     static constexpr int STAGE_OFF = NSLOT * SLOT_BYTES;
-    static constexpr int BAR_OFF = STAGE_OFF + 2 * STAGE_BYTES;
+    static constexpr int BAR_OFF = STAGE_OFF + STAGE_BYTES;
     static constexpr int WARP_BYTES = (BAR_OFF + NSLOT * 8 + 127) / 128 * 128;
     static constexpr int SMEM_BYTES = WARPS * WARP_BYTES;
 };
@@ -83,7 +87,7 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int x, int 
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
@@ -118,10 +122,16 @@ template <> __device__ __forceinline__ const Consts<float> &consts<float>(const 
 template <> __device__ __forceinline__ const Consts<double> &consts<double>(const StepParams &p) { return p.cd; }
 
 // Resident blocks per SM the register budget is sized for (shared memory allows
-// 3 blocks of the FP32 layout, 4 of the 16-bit ones, 2 of the FP64 one).
-template <typename ST> struct MinBlocks { static constexpr int value = sizeof(ST) == 2 ? 4 : (sizeof(ST) == 8 ? 2 : 3); };
+// 4 blocks of the FP32 and 16-bit layouts, 2 of the FP64 one).
+template <typename ST> struct MinBlocks { static constexpr int value = sizeof(ST) == 8 ? 2 : 4; };
 
-template <typename ST, int MODE>
+// Packed lattice velocities for runtime direction indices: bits 2a..2a+1 hold e + 1.
+constexpr uint32_t EX_PACK = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u << 8) | (2u << 10) | (0u << 12) |
+                             (0u << 14) | (2u << 16);
+constexpr uint32_t EY_PACK = (1u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (0u << 8) | (2u << 10) | (2u << 12) |
+                             (0u << 14) | (0u << 16);
+
+template <typename ST, int MODE, bool FORCED>
 __global__ void __launch_bounds__(BW, MinBlocks<ST>::value)
 stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap tin,
                       const __grid_constant__ CUtensorMap tout, const ST *__restrict__ fin)
@@ -135,6 +145,7 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
     const uint32_t ring_u32 = smem_u32(ws);
     const uint32_t stage_u32 = ring_u32 + T::STAGE_OFF;
     const uint32_t bars_u32 = ring_u32 + T::BAR_OFF;
+    ST *stage = reinterpret_cast<ST *>(ws + T::STAGE_OFF);
     const unsigned FULL = 0xffffffffu;
 
     if (lane == 0) {
@@ -144,13 +155,16 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
     __syncwarp();
 
     const Consts<R> &c = consts<R>(p);
-    const bool has_force_field = p.force != nullptr;
-    const bool uniform_forced = c.Fx != R(0) || c.Fy != R(0);
     const bool has_solid = p.solid != nullptr;
     uint32_t q_base = 0;   // sequence number of the current item's first source row (this warp)
-    int stage = 0;         // stage buffer written next
     bool abort = false;
     int issued = 0;        // item rows issued so far (lane 0)
+
+    // lane-parallel halo density: lane l < 9 handles direction l of the left
+    // halo cell, lane 16 + l of the right one
+    const int h_side = lane >> 4, h_a = lane & 15;
+    const int h_ex = h_a < 9 ? (int)((EX_PACK >> (2 * h_a)) & 3u) - 1 : 0;
+    const int h_ey = h_a < 9 ? (int)((EY_PACK >> (2 * h_a)) & 3u) - 1 : 0;
 
     const int gwarp = blockIdx.x * WARPS + warp;
     const int nwarps = gridDim.x * WARPS;
@@ -165,7 +179,9 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
         const int x = x0 + lane;
         const bool fix_left = p.perx && x0 == 0;
         const bool fix_right = p.perx && x0 + WS + 1 >= p.nx;
-        const bool fast_x = !has_solid && (p.perx || (x0 >= 2 && x0 + WS + 2 <= p.nx));
+        // full strip whose pulls (columns x0-2 .. x0+WS+1) never meet a wall or solid
+        const bool strip_fast = !has_solid && x0 + WS <= p.nx && (p.perx || (x0 >= 2 && x0 + WS + 2 <= p.nx));
+        auto row_fast = [&](int r) { return strip_fast && (p.pery || (r >= 1 && r <= p.ny - 2)); };
 
         auto slot_of = [&](int k) -> int { return (int)((q_base + (uint32_t)k) & (T::NSLOT - 1)); };
         auto row_ptr = [&](int s) -> const ST * {
@@ -210,18 +226,14 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
             }
             return true;
         };
-        // gbar(xc, r) from the ring (sources r - 1 .. r + 1 have landed)
-        auto pull = [&](int xc, int r, bool fast, R(&g)[9]) {
+        // General pull of gbar(xc, r) with walls, solids and bounce-back.
+        auto pull_general = [&](int xc, int r, R(&g)[9]) {
             const ST *rm = row_ptr(r - 1), *r0 = row_ptr(r), *rp = row_ptr(r + 1);
             const int cc = xc - x0 + T::PAD;
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
                 const int ex = cx(a), ey = cy(a);
                 const ST *src = ey > 0 ? rm : (ey < 0 ? rp : r0);
-                if (fast) {
-                    g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + cc - ex]);
-                    continue;
-                }
                 const int sx = xc - ex, sy = r - ey;
                 const bool outx = !p.perx && (sx < 0 || sx >= p.nx);
                 const bool outy = !p.pery && (sy < 0 || sy >= p.ny);
@@ -243,19 +255,48 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 }
             }
         };
-        // Post-streaming populations and density of row r: own column (lanes
-        // with x == nx on a periodic side give the wrapped column 0), and the
-        // halo columns (lane 0: x0 - 1, lane 1: x0 + WS), broadcast to all lanes.
+        // Row r (sources r - 1 .. r + 1 landed): post-streaming populations and
+        // density of the own column (lanes with x == nx on a periodic side give
+        // the wrapped column 0), and the halo densities of columns x0 - 1, x0 + WS.
         auto produce = [&](int r, R(&g)[9], bool &own_valid, R &rho_own, R &rho_l, R &rho_r) {
+            if (row_fast(r)) {
+                const ST *rm = row_ptr(r - 1), *r0 = row_ptr(r), *rp = row_ptr(r + 1);
+                const int cc = lane + T::PAD;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const ST *src = cy(a) > 0 ? rm : (cy(a) < 0 ? rp : r0);
+                    g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + cc - cx(a)]);
+                }
+                R s = g[0];
+#pragma unroll
+                for (int a = 1; a < 9; ++a) s += g[a];
+                rho_own = R(1) + s;
+                own_valid = true;
+                // halo densities: one population per lane, then a 16-lane sum
+                R v = R(0);
+                if (h_a < 9) {
+                    const ST *src = h_ey > 0 ? rm : (h_ey < 0 ? rp : r0);
+                    const int ch = (h_side ? WS : -1) + T::PAD - h_ex;
+                    v = StorageTraits<ST>::cvt(src[h_a * T::BWX + ch]);
+                }
+                v += __shfl_xor_sync(FULL, v, 8);
+                v += __shfl_xor_sync(FULL, v, 4);
+                v += __shfl_xor_sync(FULL, v, 2);
+                v += __shfl_xor_sync(FULL, v, 1);
+                rho_l = R(1) + __shfl_sync(FULL, v, 0);
+                rho_r = R(1) + __shfl_sync(FULL, v, 16);
+                return;
+            }
             const bool row_in = p.pery || (r >= 0 && r < p.ny);
             const int rw = p.pery ? wrap(r, p.ny) : r;
-            const bool fast = fast_x && (p.pery || (r >= 1 && r <= p.ny - 2));
             own_valid = false;
             rho_own = R(-1);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) g[a] = R(0);  // lanes without a cell collide the rest state
             if (row_in && (x < p.nx || (p.perx && x == p.nx))) {
                 const int xw = x < p.nx ? x : 0;
                 if (!has_solid || __ldg(p.solid + (size_t)rw * p.pitch + xw) == 0) {
-                    pull(x, r, fast, g);
+                    pull_general(x, r, g);
                     R s = g[0];
 #pragma unroll
                     for (int a = 1; a < 9; ++a) s += g[a];
@@ -271,7 +312,7 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                     const int xw = wrap(xh, p.nx);
                     if (!has_solid || __ldg(p.solid + (size_t)rw * p.pitch + xw) == 0) {
                         R gh[9];
-                        pull(xh, r, fast, gh);
+                        pull_general(xh, r, gh);
                         R s = gh[0];
 #pragma unroll
                         for (int a = 1; a < 9; ++a) s += gh[a];
@@ -313,47 +354,44 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 if (issued <= kmax) fence_proxy_async();
                 while (issued <= kmax) issue(issued++);
             }
-            // x neighbours' density (all lanes take part in the shuffles)
+            // density gradient by central differences (x neighbours by shuffles)
             R re = __shfl_down_sync(FULL, r0, 1), rw = __shfl_up_sync(FULL, r0, 1);
             if (lane == 31) re = hr0;
             if (lane == 0) rw = hl0;
-            R out[9];
-            bool wrote = false;
-            if (cur_valid) {
-                R drx = 0, dry = 0;
-                if (MODE == LBM_GI_FULL) {
-                    re = re < R(0) ? r0 : re;
-                    rw = rw < R(0) ? r0 : rw;
-                    const R rn = rp < R(0) ? r0 : rp, rs = rm < R(0) ? r0 : rm;
-                    drx = R(0.5) * (re - rw);
-                    dry = R(0.5) * (rn - rs);
-                }
-                R Fx = c.Fx, Fy = c.Fy;
-                bool forced = uniform_forced;
-                if (has_force_field) {
-                    const size_t i = (size_t)y * p.pitch + x;
+            R rn = rp, rs = rm;
+            if (!row_fast(y)) {
+                // a missing neighbour (wall side, solid) takes the cell's own density
+                re = re < R(0) ? r0 : re;
+                rw = rw < R(0) ? r0 : rw;
+                rn = rn < R(0) ? r0 : rn;
+                rs = rs < R(0) ? r0 : rs;
+            }
+            const R drx = R(0.5) * (re - rw), dry = R(0.5) * (rn - rs);
+            R Fx = R(0), Fy = R(0);
+            if (FORCED) {
+                Fx = c.Fx;
+                Fy = c.Fy;
+                if (p.force) {
+                    const size_t i = (size_t)y * p.pitch + min(x, p.nx - 1);
                     Fx = R(__ldg(p.force + i));
                     Fy = R(__ldg(p.force + (size_t)p.plane + i));
-                    forced = true;
                 }
-#pragma unroll
-                for (int a = 0; a < 9; ++a) out[a] = cur[a];
-                collide_cell<R, MODE>(out, drx, dry, Fx, Fy, forced, c, p.guard != 0, p.guard_count);
-                wrote = true;
             }
-            // stage the row: the store issued two rows ago must have read this buffer
-            if (lane == 0) bulk_wait_read_1();
-            __syncwarp();
-            ST *st = reinterpret_cast<ST *>(ws + T::STAGE_OFF + stage * T::STAGE_BYTES);
+            R out[9];
 #pragma unroll
-            for (int a = 0; a < 9; ++a) StorageTraits<ST>::store(st + a * WS + lane, wrote ? out[a] : R(0));
+            for (int a = 0; a < 9; ++a) out[a] = cur[a];
+            collide_cell<R, MODE, FORCED>(out, drx, dry, Fx, Fy, c, p.guard != 0, p.guard_count);
+            // stage the row (the previous row's store must have read the buffer)
+            if (lane == 0) bulk_wait_read_0();
+            __syncwarp();
+#pragma unroll
+            for (int a = 0; a < 9; ++a) StorageTraits<ST>::store(stage + a * WS + lane, cur_valid ? out[a] : R(0));
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) {
-                tma_store_3d(&tout, x0, y, 0, stage_u32 + stage * T::STAGE_BYTES);
+                tma_store_3d(&tout, x0, y, 0, stage_u32);
                 bulk_commit();
             }
-            stage ^= 1;
 #pragma unroll
             for (int a = 0; a < 9; ++a) cur[a] = nxt[a];
             cur_valid = nxt_valid;
@@ -383,25 +421,31 @@ cudaError_t launch_step_t(const StepParams &p, const CUtensorMap &tin, const CUt
 {
     using T = Tile<ST>;
     const ST *in = static_cast<const ST *>(fin);
+    const bool forced = p.force != nullptr || p.Fx != 0.0 || p.Fy != 0.0;
+#define LBM_LAUNCH(M, F) stream_collide_kernel<ST, M, F><<<grid, BW, T::SMEM_BYTES, s>>>(p, tin, tout, in)
     switch (p.gi_mode) {
     case LBM_GI_UNCORRECTED:
-        stream_collide_kernel<ST, LBM_GI_UNCORRECTED><<<grid, BW, T::SMEM_BYTES, s>>>(p, tin, tout, in);
+        if (forced) LBM_LAUNCH(LBM_GI_UNCORRECTED, true);
+        else LBM_LAUNCH(LBM_GI_UNCORRECTED, false);
         break;
     case LBM_GI_CUBIC_ONLY:
-        stream_collide_kernel<ST, LBM_GI_CUBIC_ONLY><<<grid, BW, T::SMEM_BYTES, s>>>(p, tin, tout, in);
+        if (forced) LBM_LAUNCH(LBM_GI_CUBIC_ONLY, true);
+        else LBM_LAUNCH(LBM_GI_CUBIC_ONLY, false);
         break;
     default:
-        stream_collide_kernel<ST, LBM_GI_FULL><<<grid, BW, T::SMEM_BYTES, s>>>(p, tin, tout, in);
+        if (forced) LBM_LAUNCH(LBM_GI_FULL, true);
+        else LBM_LAUNCH(LBM_GI_FULL, false);
         break;
     }
+#undef LBM_LAUNCH
     return cudaGetLastError();
 }
 
-template <typename ST, int MODE>
-int blocks_per_sm_mode()
+template <typename ST, int MODE, bool FORCED>
+int blocks_per_sm_variant()
 {
     using T = Tile<ST>;
-    auto fn = stream_collide_kernel<ST, MODE>;
+    auto fn = stream_collide_kernel<ST, MODE, FORCED>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM_BYTES) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -412,6 +456,16 @@ int blocks_per_sm_mode()
         return 1;
     }
     return n > 0 ? n : 1;
+}
+
+// Both force variants get the dynamic shared-memory attribute; the smaller
+// occupancy of the two is returned.
+template <typename ST, int MODE>
+int blocks_per_sm_mode()
+{
+    const int a = blocks_per_sm_variant<ST, MODE, false>();
+    const int b = blocks_per_sm_variant<ST, MODE, true>();
+    return a < b ? a : b;
 }
 
 template <typename ST>
