@@ -11,10 +11,11 @@
 
 namespace lbm {
 
-// Columns of one warp strip of the stream-collide kernel, warps per block.
-constexpr int WS = 32;
+// Columns of one warp strip of the stream-collide kernel (two per lane), warps
+// per block.
+constexpr int WS = 64;
 constexpr int WARPS = 4;
-constexpr int BW = WS * WARPS;  // threads per block
+constexpr int THREADS = 32 * WARPS;  // threads per block of the step kernel
 
 // Collision constants in the compute precision, filled on the host once per
 // launch (no FP64 arithmetic in the FP32 kernels).

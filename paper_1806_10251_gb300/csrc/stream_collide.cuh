@@ -1,8 +1,11 @@
 // Fused pull-streaming + GI preconditioned cascaded collision (one time step).
 //
-// Decomposition: every warp works on its own strip of WS = 32 columns and
-// marches up a segment of rows; warps walk the (strip, segment) items of the
-// domain independently (no block-wide barrier anywhere in the step).
+// Decomposition: every warp works on its own strip of WS = 64 columns (two
+// adjacent cells per lane) and marches up a segment of rows; warps walk the
+// (strip, segment) items of the domain independently (no block-wide barrier
+// anywhere in the step).  Two cells per lane spread the per-row work (waits,
+// copies, halo) over 64 cells and give the scheduler two independent
+// collisions per thread.
 //
 // Loads: one TMA copy (cp.async.bulk.tensor.3d, box {WS + 2 PAD, 1, 9}) brings
 // one source row of all nine population planes, with PAD halo columns on each
@@ -11,9 +14,9 @@
 // rows are in flight per warp; the pulls of Eq. 2b are shared-memory loads.
 //
 // Density gradient (same time level, central differences): each lane keeps the
-// post-streaming density of its column for rows y - 1, y, y + 1 in registers;
-// the x neighbours come from the adjacent lanes by shuffles, and two lanes
-// pull the halo columns x0 - 1 and x0 + WS.  Density entries are -1 for
+// post-streaming density of its two columns for rows y - 1, y, y + 1 in
+// registers; the x neighbours come from the same lane or the adjacent lanes by
+// shuffles, and the halo columns x0 - 1 and x0 + WS from a lane-parallel pull.  Density entries are -1 for
 // positions outside a wall side or inside a solid; the difference then uses
 // the cell's own density for that neighbour (one-sided half difference).
 //
@@ -47,7 +50,7 @@ struct Tile {
     static constexpr int BWX = WS + 2 * PAD;          // load box width (columns)
     static constexpr int ROW_BYTES = 9 * BWX * ES;    // one source row, nine planes
     static constexpr int SLOT_BYTES = (ROW_BYTES + 127) / 128 * 128;
-    static constexpr int NSLOT = 8;                   // power of two
+    static constexpr int NSLOT = ES == 8 ? 4 : 6;     // ring depth (3 rows are read at a time)
     static constexpr int STAGE_BYTES = (9 * WS * ES + 127) / 128 * 128;
     static constexpr int STAGE_OFF = NSLOT * SLOT_BYTES;
     static constexpr int BAR_OFF = STAGE_OFF + STAGE_BYTES;
@@ -122,8 +125,8 @@ template <> __device__ __forceinline__ const Consts<float> &consts<float>(const 
 template <> __device__ __forceinline__ const Consts<double> &consts<double>(const StepParams &p) { return p.cd; }
 
 // Resident blocks per SM the register budget is sized for (shared memory allows
-// 4 blocks of the FP32 and 16-bit layouts, 2 of the FP64 one).
-template <typename ST> struct MinBlocks { static constexpr int value = sizeof(ST) == 8 ? 2 : 4; };
+// 3 blocks of the FP32 layout, 5 of the 16-bit ones, 2 of the FP64 one).
+template <typename ST> struct MinBlocks { static constexpr int value = sizeof(ST) == 8 ? 2 : 3; };
 
 // Packed lattice velocities for runtime direction indices: bits 2a..2a+1 hold e + 1.
 constexpr uint32_t EX_PACK = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u << 8) | (2u << 10) | (0u << 12) |
@@ -131,8 +134,56 @@ constexpr uint32_t EX_PACK = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u
 constexpr uint32_t EY_PACK = (1u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (0u << 8) | (2u << 10) | (2u << 12) |
                              (0u << 14) | (0u << 16);
 
+// Two adjacent storage elements (even column) as one shared-memory access.
+template <typename ST> struct Pair;
+template <> struct Pair<float> {
+    using V = float2;
+    __device__ static __forceinline__ void get(const float *p, float &a, float &b)
+    {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static __forceinline__ void put(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+};
+template <> struct Pair<double> {
+    __device__ static __forceinline__ void get(const double *p, double &a, double &b)
+    {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static __forceinline__ void put(double *p, double a, double b) { *reinterpret_cast<double2 *>(p) = make_double2(a, b); }
+};
+template <> struct Pair<__half> {
+    __device__ static __forceinline__ void get(const __half *p, float &a, float &b)
+    {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static __forceinline__ void put(__half *p, float a, float b)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    __device__ static __forceinline__ void get(const __nv_bfloat16 *p, float &a, float &b)
+    {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static __forceinline__ void put(__nv_bfloat16 *p, float a, float b)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+template <bool V> struct Flag { static constexpr bool value = V; };
+
 template <typename ST, int MODE, bool FORCED>
-__global__ void __launch_bounds__(BW, MinBlocks<ST>::value)
+__global__ void __launch_bounds__(THREADS, MinBlocks<ST>::value)
 stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap tin,
                       const __grid_constant__ CUtensorMap tout, const ST *__restrict__ fin)
 {
@@ -161,7 +212,7 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
     int issued = 0;        // item rows issued so far (lane 0)
 
     // lane-parallel halo density: lane l < 9 handles direction l of the left
-    // halo cell, lane 16 + l of the right one
+    // halo cell (x0 - 1), lane 16 + l of the right one (x0 + WS)
     const int h_side = lane >> 4, h_a = lane & 15;
     const int h_ex = h_a < 9 ? (int)((EX_PACK >> (2 * h_a)) & 3u) - 1 : 0;
     const int h_ey = h_a < 9 ? (int)((EY_PACK >> (2 * h_a)) & 3u) - 1 : 0;
@@ -176,14 +227,13 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
         const int y1 = min(y0 + p.Ly, p.ny);
         const int s_first = y0 - 2;
         const int nsrc = (y1 + 1) - s_first + 1;  // source rows y0-2 .. y1+1
-        const int x = x0 + lane;
+        const int xa = x0 + 2 * lane;             // this lane's cells: xa, xa + 1
         const bool fix_left = p.perx && x0 == 0;
         const bool fix_right = p.perx && x0 + WS + 1 >= p.nx;
         // full strip whose pulls (columns x0-2 .. x0+WS+1) never meet a wall or solid
         const bool strip_fast = !has_solid && x0 + WS <= p.nx && (p.perx || (x0 >= 2 && x0 + WS + 2 <= p.nx));
-        auto row_fast = [&](int r) { return strip_fast && (p.pery || (r >= 1 && r <= p.ny - 2)); };
 
-        auto slot_of = [&](int k) -> int { return (int)((q_base + (uint32_t)k) & (T::NSLOT - 1)); };
+        auto slot_of = [&](int k) -> int { return (int)((q_base + (uint32_t)k) % T::NSLOT); };
         auto row_ptr = [&](int s) -> const ST * {
             return reinterpret_cast<const ST *>(ws + slot_of(s - s_first) * T::SLOT_BYTES);
         };
@@ -255,70 +305,83 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 }
             }
         };
-        // Row r (sources r - 1 .. r + 1 landed): post-streaming populations and
-        // density of the own column (lanes with x == nx on a periodic side give
-        // the wrapped column 0), and the halo densities of columns x0 - 1, x0 + WS.
-        auto produce = [&](int r, R(&g)[9], bool &own_valid, R &rho_own, R &rho_l, R &rho_r) {
-            if (row_fast(r)) {
+        // One cell of a general row: populations and density (-1 if none).  xc
+        // may be a halo column (-1 or nx on a periodic side): the mask is read
+        // at the wrapped column, the ring at the unwrapped one.
+        auto produce_cell = [&](int xc, int r, bool row_in, int rw, R(&g)[9], bool &valid, R &rho) {
+            valid = false;
+            rho = R(-1);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) g[a] = R(0);  // cells without a lattice site collide the rest state
+            const bool in_x = (xc >= 0 && xc < p.nx) || (p.perx && (xc == -1 || xc == p.nx));
+            if (row_in && in_x) {
+                const int xw = wrap(xc, p.nx);
+                if (!has_solid || __ldg(p.solid + (size_t)rw * p.pitch + xw) == 0) {
+                    pull_general(xc, r, g);
+                    R s = g[0];
+#pragma unroll
+                    for (int a = 1; a < 9; ++a) s += g[a];
+                    rho = R(1) + s;
+                    valid = xc >= 0 && xc < p.nx;
+                }
+            }
+        };
+        // Halo densities of columns x0 - 1 and x0 + WS in a row whose pulls are
+        // all inside: one population per lane, then a 16-lane shuffle sum.
+        auto halo_fast = [&](const ST *rm, const ST *r0, const ST *rp, R &rho_l, R &rho_r) {
+            R v = R(0);
+            if (h_a < 9) {
+                const ST *src = h_ey > 0 ? rm : (h_ey < 0 ? rp : r0);
+                const int ch = (h_side ? WS : -1) + T::PAD - h_ex;
+                v = StorageTraits<ST>::cvt(src[h_a * T::BWX + ch]);
+            }
+            v += __shfl_xor_sync(FULL, v, 8);
+            v += __shfl_xor_sync(FULL, v, 4);
+            v += __shfl_xor_sync(FULL, v, 2);
+            v += __shfl_xor_sync(FULL, v, 1);
+            rho_l = R(1) + __shfl_sync(FULL, v, 0);
+            rho_r = R(1) + __shfl_sync(FULL, v, 16);
+        };
+        // Row r (sources r - 1 .. r + 1 landed) for both cells of the lane and
+        // the halo columns.  FAST rows have no boundary logic at all.
+        auto produce = [&](auto fast_tag, int r, R(&ga)[9], R(&gb)[9], bool &va, bool &vb, R &rha, R &rhb, R &rho_l,
+                           R &rho_r) {
+            constexpr bool FAST = decltype(fast_tag)::value;
+            if (FAST) {
                 const ST *rm = row_ptr(r - 1), *r0 = row_ptr(r), *rp = row_ptr(r + 1);
-                const int cc = lane + T::PAD;
+                const int cc = 2 * lane + T::PAD;  // even: pairs are aligned
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const ST *src = cy(a) > 0 ? rm : (cy(a) < 0 ? rp : r0);
-                    g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + cc - cx(a)]);
+                    const ST *q = src + a * T::BWX + cc - cx(a);
+                    if (cx(a) == 0) {
+                        Pair<ST>::get(q, ga[a], gb[a]);
+                    } else {
+                        ga[a] = StorageTraits<ST>::cvt(q[0]);
+                        gb[a] = StorageTraits<ST>::cvt(q[1]);
+                    }
                 }
-                R s = g[0];
+                R sa = ga[0], sb = gb[0];
 #pragma unroll
-                for (int a = 1; a < 9; ++a) s += g[a];
-                rho_own = R(1) + s;
-                own_valid = true;
-                // halo densities: one population per lane, then a 16-lane sum
-                R v = R(0);
-                if (h_a < 9) {
-                    const ST *src = h_ey > 0 ? rm : (h_ey < 0 ? rp : r0);
-                    const int ch = (h_side ? WS : -1) + T::PAD - h_ex;
-                    v = StorageTraits<ST>::cvt(src[h_a * T::BWX + ch]);
+                for (int a = 1; a < 9; ++a) {
+                    sa += ga[a];
+                    sb += gb[a];
                 }
-                v += __shfl_xor_sync(FULL, v, 8);
-                v += __shfl_xor_sync(FULL, v, 4);
-                v += __shfl_xor_sync(FULL, v, 2);
-                v += __shfl_xor_sync(FULL, v, 1);
-                rho_l = R(1) + __shfl_sync(FULL, v, 0);
-                rho_r = R(1) + __shfl_sync(FULL, v, 16);
+                rha = R(1) + sa;
+                rhb = R(1) + sb;
+                va = vb = true;
+                halo_fast(rm, r0, rp, rho_l, rho_r);
                 return;
             }
             const bool row_in = p.pery || (r >= 0 && r < p.ny);
             const int rw = p.pery ? wrap(r, p.ny) : r;
-            own_valid = false;
-            rho_own = R(-1);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) g[a] = R(0);  // lanes without a cell collide the rest state
-            if (row_in && (x < p.nx || (p.perx && x == p.nx))) {
-                const int xw = x < p.nx ? x : 0;
-                if (!has_solid || __ldg(p.solid + (size_t)rw * p.pitch + xw) == 0) {
-                    pull_general(x, r, g);
-                    R s = g[0];
-#pragma unroll
-                    for (int a = 1; a < 9; ++a) s += g[a];
-                    rho_own = R(1) + s;
-                    own_valid = x < p.nx;
-                }
-            }
+            produce_cell(xa, r, row_in, rw, ga, va, rha);
+            produce_cell(xa + 1, r, row_in, rw, gb, vb, rhb);
             R rho_h = R(-1);
             if (lane < 2) {
-                const int xh = lane == 0 ? x0 - 1 : x0 + WS;
-                const bool need = lane == 0 ? (x0 >= 1 || p.perx) : (xh < p.nx || (p.perx && xh == p.nx));
-                if (row_in && need) {
-                    const int xw = wrap(xh, p.nx);
-                    if (!has_solid || __ldg(p.solid + (size_t)rw * p.pitch + xw) == 0) {
-                        R gh[9];
-                        pull_general(xh, r, gh);
-                        R s = gh[0];
-#pragma unroll
-                        for (int a = 1; a < 9; ++a) s += gh[a];
-                        rho_h = R(1) + s;
-                    }
-                }
+                R gh[9];
+                bool vh;
+                produce_cell(lane == 0 ? x0 - 1 : x0 + WS, r, row_in, rw, gh, vh, rho_h);
             }
             rho_l = __shfl_sync(FULL, rho_h, 0);
             rho_r = __shfl_sync(FULL, rho_h, 1);
@@ -334,19 +397,32 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
             abort = true;
             break;
         }
-        R cur[9], nxt[9];
-        bool cur_valid, nxt_valid;
-        R rm, r0, rp, hl0, hr0, hlp, hrp, dummy_l, dummy_r;
-        produce(y0 - 1, nxt, nxt_valid, rm, dummy_l, dummy_r);
-        produce(y0, cur, cur_valid, r0, hl0, hr0);
+        // rows in flight: cur = row y, nxt = row y + 1; densities of rows y-1, y, y+1
+        R ca[9], cb[9], na[9], nb[9];
+        bool cva, cvb, nva, nvb;
+        R rma, rmb, r0a, r0b, rpa, rpb, hl0, hr0, hlp, hrp, d0, d1;
+        auto produce_any = [&](int r, R(&ga)[9], R(&gb)[9], bool &va, bool &vb, R &rha, R &rhb, R &rho_l, R &rho_r) {
+            if (strip_fast && (p.pery || (r >= 1 && r <= p.ny - 2)))
+                produce(Flag<true>(), r, ga, gb, va, vb, rha, rhb, rho_l, rho_r);
+            else
+                produce(Flag<false>(), r, ga, gb, va, vb, rha, rhb, rho_l, rho_r);
+        };
+        produce_any(y0 - 1, na, nb, nva, nvb, rma, rmb, d0, d1);
+        produce_any(y0, ca, cb, cva, cvb, r0a, r0b, hl0, hr0);
+        __syncwarp();
+        if (lane == 0) {
+            // source row y0 - 2 is no longer read: refill its slot
+            const int kmax = min(nsrc - 1, T::NSLOT);
+            if (issued <= kmax) fence_proxy_async();
+            while (issued <= kmax) issue(issued++);
+        }
 
-        for (int y = y0; y < y1; ++y) {
+        // One time-step row: land source y + 2, produce row y + 1, collide row y.
+        auto iter = [&](auto fast_tag, int y) -> bool {
+            constexpr bool FAST = decltype(fast_tag)::value;
             const int kl = y - y0 + 4;  // source row y + 2
-            if (kl < nsrc && !land(kl)) {
-                abort = true;
-                break;
-            }
-            produce(y + 1, nxt, nxt_valid, rp, hlp, hrp);
+            if (kl < nsrc && !land(kl)) return false;
+            produce(fast_tag, y + 1, na, nb, nva, nvb, rpa, rpb, hlp, hrp);
             __syncwarp();
             if (lane == 0) {
                 // source rows up to y are no longer read: refill their slots
@@ -354,38 +430,51 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 if (issued <= kmax) fence_proxy_async();
                 while (issued <= kmax) issue(issued++);
             }
-            // density gradient by central differences (x neighbours by shuffles)
-            R re = __shfl_down_sync(FULL, r0, 1), rw = __shfl_up_sync(FULL, r0, 1);
-            if (lane == 31) re = hr0;
-            if (lane == 0) rw = hl0;
-            R rn = rp, rs = rm;
-            if (!row_fast(y)) {
+            // density gradient by central differences
+            R wa = __shfl_up_sync(FULL, r0b, 1), eb = __shfl_down_sync(FULL, r0a, 1);
+            if (lane == 0) wa = hl0;
+            if (lane == 31) eb = hr0;
+            R ea = r0b, wb = r0a, na_ = rpa, sa_ = rma, nb_ = rpb, sb_ = rmb;
+            if (!FAST) {
                 // a missing neighbour (wall side, solid) takes the cell's own density
-                re = re < R(0) ? r0 : re;
-                rw = rw < R(0) ? r0 : rw;
-                rn = rn < R(0) ? r0 : rn;
-                rs = rs < R(0) ? r0 : rs;
+                wa = wa < R(0) ? r0a : wa;
+                ea = ea < R(0) ? r0a : ea;
+                na_ = na_ < R(0) ? r0a : na_;
+                sa_ = sa_ < R(0) ? r0a : sa_;
+                wb = wb < R(0) ? r0b : wb;
+                eb = eb < R(0) ? r0b : eb;
+                nb_ = nb_ < R(0) ? r0b : nb_;
+                sb_ = sb_ < R(0) ? r0b : sb_;
             }
-            const R drx = R(0.5) * (re - rw), dry = R(0.5) * (rn - rs);
-            R Fx = R(0), Fy = R(0);
+            R Fxa = R(0), Fya = R(0), Fxb = R(0), Fyb = R(0);
             if (FORCED) {
-                Fx = c.Fx;
-                Fy = c.Fy;
+                Fxa = Fxb = c.Fx;
+                Fya = Fyb = c.Fy;
                 if (p.force) {
-                    const size_t i = (size_t)y * p.pitch + min(x, p.nx - 1);
-                    Fx = R(__ldg(p.force + i));
-                    Fy = R(__ldg(p.force + (size_t)p.plane + i));
+                    const size_t i = (size_t)y * p.pitch + min(xa, p.nx - 1);
+                    const size_t j = (size_t)y * p.pitch + min(xa + 1, p.nx - 1);
+                    Fxa = R(__ldg(p.force + i));
+                    Fya = R(__ldg(p.force + (size_t)p.plane + i));
+                    Fxb = R(__ldg(p.force + j));
+                    Fyb = R(__ldg(p.force + (size_t)p.plane + j));
                 }
             }
-            R out[9];
+            R oa[9], ob[9];
 #pragma unroll
-            for (int a = 0; a < 9; ++a) out[a] = cur[a];
-            collide_cell<R, MODE, FORCED>(out, drx, dry, Fx, Fy, c, p.guard != 0, p.guard_count);
+            for (int a = 0; a < 9; ++a) {
+                oa[a] = ca[a];
+                ob[a] = cb[a];
+            }
+            collide_cell<R, MODE, FORCED>(oa, R(0.5) * (ea - wa), R(0.5) * (na_ - sa_), Fxa, Fya, c, p.guard != 0,
+                                          p.guard_count);
+            collide_cell<R, MODE, FORCED>(ob, R(0.5) * (eb - wb), R(0.5) * (nb_ - sb_), Fxb, Fyb, c, p.guard != 0,
+                                          p.guard_count);
             // stage the row (the previous row's store must have read the buffer)
             if (lane == 0) bulk_wait_read_0();
             __syncwarp();
 #pragma unroll
-            for (int a = 0; a < 9; ++a) StorageTraits<ST>::store(stage + a * WS + lane, cur_valid ? out[a] : R(0));
+            for (int a = 0; a < 9; ++a)
+                Pair<ST>::put(stage + a * WS + 2 * lane, (FAST || cva) ? oa[a] : R(0), (FAST || cvb) ? ob[a] : R(0));
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) {
@@ -393,13 +482,30 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 bulk_commit();
             }
 #pragma unroll
-            for (int a = 0; a < 9; ++a) cur[a] = nxt[a];
-            cur_valid = nxt_valid;
-            rm = r0;
-            r0 = rp;
+            for (int a = 0; a < 9; ++a) {
+                ca[a] = na[a];
+                cb[a] = nb[a];
+            }
+            cva = nva;
+            cvb = nvb;
+            rma = r0a;
+            rmb = r0b;
+            r0a = rpa;
+            r0b = rpb;
             hl0 = hlp;
             hr0 = hrp;
+            return true;
+        };
+        // rows whose iteration is boundary-free: y and y + 1 both fast rows
+        int yf0 = y1, yf1 = y1;
+        if (strip_fast) {
+            yf0 = p.pery ? y0 : max(y0, 1);
+            yf1 = p.pery ? y1 : min(y1, p.ny - 2);
+            if (yf1 < yf0) yf0 = yf1 = y1;
         }
+        for (int y = y0; y < yf0 && !abort; ++y) abort = !iter(Flag<false>(), y);
+        for (int y = yf0; y < yf1 && !abort; ++y) abort = !iter(Flag<true>(), y);
+        for (int y = max(yf1, yf0); y < y1 && !abort; ++y) abort = !iter(Flag<false>(), y);
         if (abort) break;
         q_base += (uint32_t)nsrc;
     }
@@ -407,8 +513,8 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
         // record the failure and let this warp's copies in flight finish
         atomicExch(p.error, 1);
         for (int k = max(0, issued - T::NSLOT); k < issued; ++k) {
-            const uint32_t parity = ((q_base + (uint32_t)k) / T::NSLOT) & 1u;
-            if (!mbar_wait_bounded(bars_u32 + 8 * ((q_base + (uint32_t)k) & (T::NSLOT - 1)), parity)) break;
+            const uint32_t q = q_base + (uint32_t)k;
+            if (!mbar_wait_bounded(bars_u32 + 8 * (q % T::NSLOT), (q / T::NSLOT) & 1u)) break;
         }
     }
     if (lane == 0) bulk_wait_all();  // stores done before the stage memory goes away
@@ -422,7 +528,7 @@ cudaError_t launch_step_t(const StepParams &p, const CUtensorMap &tin, const CUt
     using T = Tile<ST>;
     const ST *in = static_cast<const ST *>(fin);
     const bool forced = p.force != nullptr || p.Fx != 0.0 || p.Fy != 0.0;
-#define LBM_LAUNCH(M, F) stream_collide_kernel<ST, M, F><<<grid, BW, T::SMEM_BYTES, s>>>(p, tin, tout, in)
+#define LBM_LAUNCH(M, F) stream_collide_kernel<ST, M, F><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, tout, in)
     switch (p.gi_mode) {
     case LBM_GI_UNCORRECTED:
         if (forced) LBM_LAUNCH(LBM_GI_UNCORRECTED, true);
@@ -451,7 +557,7 @@ int blocks_per_sm_variant()
         return 1;
     }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, BW, T::SMEM_BYTES) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, THREADS, T::SMEM_BYTES) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
