@@ -158,17 +158,19 @@ __device__ __forceinline__ void collide_cell(R (&g)[9], R drx, R dry, R Fx, R Fy
 
     // f~ = fbar + K g^ (columns: K3 = 3|e^2| - 4, K4 = |ex^2 - ey^2|, K5 = |ex ey|,
     // K6 = -3|ex^2 ey| + 2|ey|, K7 = -3|ex ey^2| + 2|ex|, K8 = 9|ex^2 ey^2| - 6|e^2| + 4)
-    const R d8 = R(2) * g8;
+    const R a14 = -(g3 + R(2) * g8);  // common to directions 1..4
+    const R b13 = a14 + g4, b24 = a14 - g4;
     g[0] += R(4) * (g8 - g3);
-    g[1] += -g3 + g4 + R(2) * g7 - d8;
-    g[2] += -g3 - g4 + R(2) * g6 - d8;
-    g[3] += -g3 + g4 - R(2) * g7 - d8;
-    g[4] += -g3 - g4 - R(2) * g6 - d8;
-    const R h = R(2) * g3 + g8;
-    g[5] += h + g5 - g6 - g7;
-    g[6] += h - g5 - g6 + g7;
-    g[7] += h + g5 + g6 + g7;
-    g[8] += h - g5 + g6 - g7;
+    g[1] += b13 + R(2) * g7;
+    g[3] += b13 - R(2) * g7;
+    g[2] += b24 + R(2) * g6;
+    g[4] += b24 - R(2) * g6;
+    const R h = R(2) * g3 + g8;       // common to directions 5..8
+    const R hp = h + g5, hm = h - g5, s67 = g6 + g7, d67 = g6 - g7;
+    g[5] += hp - s67;
+    g[7] += hp + s67;
+    g[6] += hm - d67;
+    g[8] += hm + d67;
 
     if (forced) {
         // S = T^-1 sigma' (inverse of the Eq. 5 map), sigma'_0 = 0

@@ -11,9 +11,9 @@
 
 namespace lbm {
 
-// Columns of one warp strip of the stream-collide kernel (two per lane), warps
+// Columns of one warp strip of the stream-collide kernel (one per lane), warps
 // per block.
-constexpr int WS = 64;
+constexpr int WS = 32;
 constexpr int WARPS = 4;
 constexpr int THREADS = 32 * WARPS;  // threads per block of the step kernel
 

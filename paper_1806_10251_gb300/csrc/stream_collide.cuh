@@ -1,11 +1,9 @@
 // Fused pull-streaming + GI preconditioned cascaded collision (one time step).
 //
-// Decomposition: every warp works on its own strip of WS = 64 columns (two
-// adjacent cells per lane) and marches up a segment of rows; warps walk the
-// (strip, segment) items of the domain independently (no block-wide barrier
-// anywhere in the step).  Two cells per lane spread the per-row work (waits,
-// copies, halo) over 64 cells and give the scheduler two independent
-// collisions per thread.
+// Decomposition: every warp works on its own strip of WS = 32 columns (one
+// cell per lane) and marches up a segment of rows; warps walk the (strip,
+// segment) items of the domain independently (no block-wide barrier anywhere
+// in the step).
 //
 // Loads: one TMA copy (cp.async.bulk.tensor.3d, box {WS + 2 PAD, 1, 9}) brings
 // one source row of all nine population planes, with PAD halo columns on each
@@ -14,9 +12,9 @@
 // rows are in flight per warp; the pulls of Eq. 2b are shared-memory loads.
 //
 // Density gradient (same time level, central differences): each lane keeps the
-// post-streaming density of its two columns for rows y - 1, y, y + 1 in
-// registers; the x neighbours come from the same lane or the adjacent lanes by
-// shuffles, and the halo columns x0 - 1 and x0 + WS from a lane-parallel pull.  Density entries are -1 for
+// post-streaming density of its column for rows y - 1, y, y + 1 in registers;
+// the x neighbours come from the adjacent lanes by shuffles, and the halo
+// columns x0 - 1 and x0 + WS from a lane-parallel pull.  Density entries are -1 for
 // positions outside a wall side or inside a solid; the difference then uses
 // the cell's own density for that neighbour (one-sided half difference).
 //
@@ -50,7 +48,7 @@ struct Tile {
     static constexpr int BWX = WS + 2 * PAD;          // load box width (columns)
     static constexpr int ROW_BYTES = 9 * BWX * ES;    // one source row, nine planes
     static constexpr int SLOT_BYTES = (ROW_BYTES + 127) / 128 * 128;
-    static constexpr int NSLOT = ES == 8 ? 4 : 6;     // ring depth (3 rows are read at a time)
+    static constexpr int NSLOT = ES == 8 ? 6 : 8;     // ring depth (3 rows are read at a time)
     static constexpr int STAGE_BYTES = (9 * WS * ES + 127) / 128 * 128;
     static constexpr int STAGE_OFF = NSLOT * SLOT_BYTES;
     static constexpr int BAR_OFF = STAGE_OFF + STAGE_BYTES;
@@ -125,60 +123,14 @@ template <> __device__ __forceinline__ const Consts<float> &consts<float>(const 
 template <> __device__ __forceinline__ const Consts<double> &consts<double>(const StepParams &p) { return p.cd; }
 
 // Resident blocks per SM the register budget is sized for (shared memory allows
-// 3 blocks of the FP32 layout, 5 of the 16-bit ones, 2 of the FP64 one).
-template <typename ST> struct MinBlocks { static constexpr int value = sizeof(ST) == 8 ? 2 : 3; };
+// 4 blocks of the FP32 layout, more of the 16-bit ones, 2 of the FP64 one).
+template <typename ST> struct MinBlocks { static constexpr int value = sizeof(ST) == 8 ? 2 : 4; };
 
 // Packed lattice velocities for runtime direction indices: bits 2a..2a+1 hold e + 1.
 constexpr uint32_t EX_PACK = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u << 8) | (2u << 10) | (0u << 12) |
                              (0u << 14) | (2u << 16);
 constexpr uint32_t EY_PACK = (1u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (0u << 8) | (2u << 10) | (2u << 12) |
                              (0u << 14) | (0u << 16);
-
-// Two adjacent storage elements (even column) as one shared-memory access.
-template <typename ST> struct Pair;
-template <> struct Pair<float> {
-    using V = float2;
-    __device__ static __forceinline__ void get(const float *p, float &a, float &b)
-    {
-        const float2 v = *reinterpret_cast<const float2 *>(p);
-        a = v.x;
-        b = v.y;
-    }
-    __device__ static __forceinline__ void put(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
-};
-template <> struct Pair<double> {
-    __device__ static __forceinline__ void get(const double *p, double &a, double &b)
-    {
-        const double2 v = *reinterpret_cast<const double2 *>(p);
-        a = v.x;
-        b = v.y;
-    }
-    __device__ static __forceinline__ void put(double *p, double a, double b) { *reinterpret_cast<double2 *>(p) = make_double2(a, b); }
-};
-template <> struct Pair<__half> {
-    __device__ static __forceinline__ void get(const __half *p, float &a, float &b)
-    {
-        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
-        a = v.x;
-        b = v.y;
-    }
-    __device__ static __forceinline__ void put(__half *p, float a, float b)
-    {
-        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
-    }
-};
-template <> struct Pair<__nv_bfloat16> {
-    __device__ static __forceinline__ void get(const __nv_bfloat16 *p, float &a, float &b)
-    {
-        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
-        a = v.x;
-        b = v.y;
-    }
-    __device__ static __forceinline__ void put(__nv_bfloat16 *p, float a, float b)
-    {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
-    }
-};
 
 template <bool V> struct Flag { static constexpr bool value = V; };
 
@@ -227,7 +179,7 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
         const int y1 = min(y0 + p.Ly, p.ny);
         const int s_first = y0 - 2;
         const int nsrc = (y1 + 1) - s_first + 1;  // source rows y0-2 .. y1+1
-        const int xa = x0 + 2 * lane;             // this lane's cells: xa, xa + 1
+        const int x = x0 + lane;                  // this lane's cell
         const bool fix_left = p.perx && x0 == 0;
         const bool fix_right = p.perx && x0 + WS + 1 >= p.nx;
         // full strip whose pulls (columns x0-2 .. x0+WS+1) never meet a wall or solid
@@ -342,41 +294,29 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
             rho_l = R(1) + __shfl_sync(FULL, v, 0);
             rho_r = R(1) + __shfl_sync(FULL, v, 16);
         };
-        // Row r (sources r - 1 .. r + 1 landed) for both cells of the lane and
-        // the halo columns.  FAST rows have no boundary logic at all.
-        auto produce = [&](auto fast_tag, int r, R(&ga)[9], R(&gb)[9], bool &va, bool &vb, R &rha, R &rhb, R &rho_l,
-                           R &rho_r) {
+        // Row r (sources r - 1 .. r + 1 landed) for the lane's cell and the halo
+        // columns.  FAST rows have no boundary logic at all.
+        auto produce = [&](auto fast_tag, int r, R(&g)[9], bool &valid, R &rho, R &rho_l, R &rho_r) {
             constexpr bool FAST = decltype(fast_tag)::value;
             if (FAST) {
                 const ST *rm = row_ptr(r - 1), *r0 = row_ptr(r), *rp = row_ptr(r + 1);
-                const int cc = 2 * lane + T::PAD;  // even: pairs are aligned
+                const int cc = lane + T::PAD;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const ST *src = cy(a) > 0 ? rm : (cy(a) < 0 ? rp : r0);
-                    const ST *q = src + a * T::BWX + cc - cx(a);
-                    if (cx(a) == 0) {
-                        Pair<ST>::get(q, ga[a], gb[a]);
-                    } else {
-                        ga[a] = StorageTraits<ST>::cvt(q[0]);
-                        gb[a] = StorageTraits<ST>::cvt(q[1]);
-                    }
+                    g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + cc - cx(a)]);
                 }
-                R sa = ga[0], sb = gb[0];
+                R s = g[0];
 #pragma unroll
-                for (int a = 1; a < 9; ++a) {
-                    sa += ga[a];
-                    sb += gb[a];
-                }
-                rha = R(1) + sa;
-                rhb = R(1) + sb;
-                va = vb = true;
+                for (int a = 1; a < 9; ++a) s += g[a];
+                rho = R(1) + s;
+                valid = true;
                 halo_fast(rm, r0, rp, rho_l, rho_r);
                 return;
             }
             const bool row_in = p.pery || (r >= 0 && r < p.ny);
             const int rw = p.pery ? wrap(r, p.ny) : r;
-            produce_cell(xa, r, row_in, rw, ga, va, rha);
-            produce_cell(xa + 1, r, row_in, rw, gb, vb, rhb);
+            produce_cell(x, r, row_in, rw, g, valid, rho);
             R rho_h = R(-1);
             if (lane < 2) {
                 R gh[9];
@@ -397,18 +337,18 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
             abort = true;
             break;
         }
-        // rows in flight: cur = row y, nxt = row y + 1; densities of rows y-1, y, y+1
-        R ca[9], cb[9], na[9], nb[9];
-        bool cva, cvb, nva, nvb;
-        R rma, rmb, r0a, r0b, rpa, rpb, hl0, hr0, hlp, hrp, d0, d1;
-        auto produce_any = [&](int r, R(&ga)[9], R(&gb)[9], bool &va, bool &vb, R &rha, R &rhb, R &rho_l, R &rho_r) {
+        // cur = populations of row y, nxt = row y + 1; densities of rows y-1, y, y+1
+        R cur[9], nxt[9];
+        bool cur_valid, nxt_valid;
+        R rm, r0, rp, hl0, hr0, hlp, hrp, d0, d1;
+        auto produce_any = [&](int r, R(&g)[9], bool &valid, R &rho, R &rho_l, R &rho_r) {
             if (strip_fast && (p.pery || (r >= 1 && r <= p.ny - 2)))
-                produce(Flag<true>(), r, ga, gb, va, vb, rha, rhb, rho_l, rho_r);
+                produce(Flag<true>(), r, g, valid, rho, rho_l, rho_r);
             else
-                produce(Flag<false>(), r, ga, gb, va, vb, rha, rhb, rho_l, rho_r);
+                produce(Flag<false>(), r, g, valid, rho, rho_l, rho_r);
         };
-        produce_any(y0 - 1, na, nb, nva, nvb, rma, rmb, d0, d1);
-        produce_any(y0, ca, cb, cva, cvb, r0a, r0b, hl0, hr0);
+        produce_any(y0 - 1, nxt, nxt_valid, rm, d0, d1);
+        produce_any(y0, cur, cur_valid, r0, hl0, hr0);
         __syncwarp();
         if (lane == 0) {
             // source row y0 - 2 is no longer read: refill its slot
@@ -422,7 +362,7 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
             constexpr bool FAST = decltype(fast_tag)::value;
             const int kl = y - y0 + 4;  // source row y + 2
             if (kl < nsrc && !land(kl)) return false;
-            produce(fast_tag, y + 1, na, nb, nva, nvb, rpa, rpb, hlp, hrp);
+            produce(fast_tag, y + 1, nxt, nxt_valid, rp, hlp, hrp);
             __syncwarp();
             if (lane == 0) {
                 // source rows up to y are no longer read: refill their slots
@@ -430,51 +370,39 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 if (issued <= kmax) fence_proxy_async();
                 while (issued <= kmax) issue(issued++);
             }
-            // density gradient by central differences
-            R wa = __shfl_up_sync(FULL, r0b, 1), eb = __shfl_down_sync(FULL, r0a, 1);
-            if (lane == 0) wa = hl0;
-            if (lane == 31) eb = hr0;
-            R ea = r0b, wb = r0a, na_ = rpa, sa_ = rma, nb_ = rpb, sb_ = rmb;
+            // density gradient by central differences (x neighbours by shuffles)
+            R re = __shfl_down_sync(FULL, r0, 1), rw = __shfl_up_sync(FULL, r0, 1);
+            if (lane == 31) re = hr0;
+            if (lane == 0) rw = hl0;
+            R rn = rp, rs = rm;
             if (!FAST) {
                 // a missing neighbour (wall side, solid) takes the cell's own density
-                wa = wa < R(0) ? r0a : wa;
-                ea = ea < R(0) ? r0a : ea;
-                na_ = na_ < R(0) ? r0a : na_;
-                sa_ = sa_ < R(0) ? r0a : sa_;
-                wb = wb < R(0) ? r0b : wb;
-                eb = eb < R(0) ? r0b : eb;
-                nb_ = nb_ < R(0) ? r0b : nb_;
-                sb_ = sb_ < R(0) ? r0b : sb_;
+                re = re < R(0) ? r0 : re;
+                rw = rw < R(0) ? r0 : rw;
+                rn = rn < R(0) ? r0 : rn;
+                rs = rs < R(0) ? r0 : rs;
             }
-            R Fxa = R(0), Fya = R(0), Fxb = R(0), Fyb = R(0);
+            R Fx = R(0), Fy = R(0);
             if (FORCED) {
-                Fxa = Fxb = c.Fx;
-                Fya = Fyb = c.Fy;
+                Fx = c.Fx;
+                Fy = c.Fy;
                 if (p.force) {
-                    const size_t i = (size_t)y * p.pitch + min(xa, p.nx - 1);
-                    const size_t j = (size_t)y * p.pitch + min(xa + 1, p.nx - 1);
-                    Fxa = R(__ldg(p.force + i));
-                    Fya = R(__ldg(p.force + (size_t)p.plane + i));
-                    Fxb = R(__ldg(p.force + j));
-                    Fyb = R(__ldg(p.force + (size_t)p.plane + j));
+                    const size_t i = (size_t)y * p.pitch + min(x, p.nx - 1);
+                    Fx = R(__ldg(p.force + i));
+                    Fy = R(__ldg(p.force + (size_t)p.plane + i));
                 }
             }
-            R oa[9], ob[9];
+            R out[9];
 #pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                oa[a] = ca[a];
-                ob[a] = cb[a];
-            }
-            collide_cell<R, MODE, FORCED>(oa, R(0.5) * (ea - wa), R(0.5) * (na_ - sa_), Fxa, Fya, c, p.guard != 0,
-                                          p.guard_count);
-            collide_cell<R, MODE, FORCED>(ob, R(0.5) * (eb - wb), R(0.5) * (nb_ - sb_), Fxb, Fyb, c, p.guard != 0,
+            for (int a = 0; a < 9; ++a) out[a] = cur[a];
+            collide_cell<R, MODE, FORCED>(out, R(0.5) * (re - rw), R(0.5) * (rn - rs), Fx, Fy, c, p.guard != 0,
                                           p.guard_count);
             // stage the row (the previous row's store must have read the buffer)
             if (lane == 0) bulk_wait_read_0();
             __syncwarp();
 #pragma unroll
             for (int a = 0; a < 9; ++a)
-                Pair<ST>::put(stage + a * WS + 2 * lane, (FAST || cva) ? oa[a] : R(0), (FAST || cvb) ? ob[a] : R(0));
+                StorageTraits<ST>::store(stage + a * WS + lane, (FAST || cur_valid) ? out[a] : R(0));
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) {
@@ -482,16 +410,10 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 bulk_commit();
             }
 #pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                ca[a] = na[a];
-                cb[a] = nb[a];
-            }
-            cva = nva;
-            cvb = nvb;
-            rma = r0a;
-            rmb = r0b;
-            r0a = rpa;
-            r0b = rpb;
+            for (int a = 0; a < 9; ++a) cur[a] = nxt[a];
+            cur_valid = nxt_valid;
+            rm = r0;
+            r0 = rp;
             hl0 = hlp;
             hr0 = hrp;
             return true;
