@@ -131,6 +131,9 @@ constexpr uint32_t EX_PACK = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u
                              (0u << 14) | (2u << 16);
 constexpr uint32_t EY_PACK = (1u << 0) | (1u << 2) | (2u << 4) | (1u << 6) | (0u << 8) | (2u << 10) | (2u << 12) |
                              (0u << 14) | (0u << 16);
+// opposite directions, 4 bits each: 0 3 4 1 2 7 8 5 6
+constexpr uint64_t OPP_PACK = 0ull | (3ull << 4) | (4ull << 8) | (1ull << 12) | (2ull << 16) | (7ull << 20) |
+                              (8ull << 24) | (5ull << 28) | (6ull << 32);
 
 template <bool V> struct Flag { static constexpr bool value = V; };
 
@@ -278,27 +281,31 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 }
             }
         };
-        // Halo densities of columns x0 - 1 and x0 + WS in a row whose pulls are
-        // all inside: one population per lane, then a 16-lane shuffle sum.
-        auto halo_fast = [&](const ST *rm, const ST *r0, const ST *rp, R &rho_l, R &rho_r) {
-            R v = R(0);
-            if (h_a < 9) {
-                const ST *src = h_ey > 0 ? rm : (h_ey < 0 ? rp : r0);
-                const int ch = (h_side ? WS : -1) + T::PAD - h_ex;
-                v = StorageTraits<ST>::cvt(src[h_a * T::BWX + ch]);
-            }
-            v += __shfl_xor_sync(FULL, v, 8);
-            v += __shfl_xor_sync(FULL, v, 4);
-            v += __shfl_xor_sync(FULL, v, 2);
-            v += __shfl_xor_sync(FULL, v, 1);
-            rho_l = R(1) + __shfl_sync(FULL, v, 0);
-            rho_r = R(1) + __shfl_sync(FULL, v, 16);
+        // Moving-wall term of half-way bounce-back for direction a whose source
+        // (sx, sy) lies beyond the outx / outy side(s): 6 w_a rho0 (e_a . u_w);
+        // a source beyond two sides (a corner) sees a stationary wall.
+        auto bb_term = [&](int a, int ex, int ey, int sx, int sy, bool outx, bool outy) -> R {
+            if (outx == outy) return R(0);
+            const int side = outx ? (sx < 0 ? 0 : 1) : (sy < 0 ? 2 : 3);
+            const R w = a == 0 ? R(4.0 / 9.0) : (a <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+            return w * (R(ex) * c.wall6[side][0] + R(ey) * c.wall6[side][1]);
         };
         // Row r (sources r - 1 .. r + 1 landed) for the lane's cell and the halo
-        // columns.  FAST rows have no boundary logic at all.
+        // columns.  FAST rows have no boundary logic at all; other rows of
+        // domains without solids load like FAST rows and let only the lanes on
+        // a wall cell (and the halo lanes) replace the populations whose
+        // source lies beyond the wall; domains with solids take the general path.
         auto produce = [&](auto fast_tag, int r, R(&g)[9], bool &valid, R &rho, R &rho_l, R &rho_r) {
             constexpr bool FAST = decltype(fast_tag)::value;
-            if (FAST) {
+            if (FAST || !has_solid) {
+                const bool row_in = FAST || p.pery || (r >= 0 && r < p.ny);
+                if (!row_in) {
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) g[a] = R(0);
+                    valid = false;
+                    rho = rho_l = rho_r = R(-1);
+                    return;
+                }
                 const ST *rm = row_ptr(r - 1), *r0 = row_ptr(r), *rp = row_ptr(r + 1);
                 const int cc = lane + T::PAD;
 #pragma unroll
@@ -306,12 +313,64 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                     const ST *src = cy(a) > 0 ? rm : (cy(a) < 0 ? rp : r0);
                     g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + cc - cx(a)]);
                 }
-                R s = g[0];
+                bool own = true;
+                if (!FAST) {
+                    own = x < p.nx || (p.perx && x == p.nx);
+                    const bool near = own && ((!p.perx && (x == 0 || x == p.nx - 1)) ||
+                                              (!p.pery && (r == 0 || r == p.ny - 1)));
+                    if (near) {
 #pragma unroll
-                for (int a = 1; a < 9; ++a) s += g[a];
-                rho = R(1) + s;
-                valid = true;
-                halo_fast(rm, r0, rp, rho_l, rho_r);
+                        for (int a = 1; a < 9; ++a) {
+                            const int ex = cx(a), ey = cy(a), sx = x - ex, sy = r - ey;
+                            const bool outx = !p.perx && (sx < 0 || sx >= p.nx);
+                            const bool outy = !p.pery && (sy < 0 || sy >= p.ny);
+                            if (outx || outy)
+                                g[a] = StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + cc]) +
+                                       bb_term(a, ex, ey, sx, sy, outx, outy);
+                        }
+                    }
+                }
+                if (own) {
+                    R s = g[0];
+#pragma unroll
+                    for (int a = 1; a < 9; ++a) s += g[a];
+                    rho = R(1) + s;
+                    valid = FAST || x < p.nx;
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) g[a] = R(0);  // no lattice site: collide the rest state
+                    rho = R(-1);
+                    valid = false;
+                }
+                // halo densities: one population per lane, then a 16-lane sum
+                const bool need_l = FAST || x0 >= 1 || p.perx;
+                const bool need_r = FAST || x0 + WS < p.nx || (p.perx && x0 + WS == p.nx);
+                R v = R(0);
+                if (h_a < 9 && (h_side ? need_r : need_l)) {
+                    const int xh = h_side ? x0 + WS : x0 - 1;
+                    const int ch = xh - x0 + T::PAD;
+                    const ST *src = h_ey > 0 ? rm : (h_ey < 0 ? rp : r0);
+                    bool out = false;
+                    if (!FAST) {
+                        const int sx = xh - h_ex, sy = r - h_ey;
+                        const bool outx = !p.perx && (sx < 0 || sx >= p.nx);
+                        const bool outy = !p.pery && (sy < 0 || sy >= p.ny);
+                        if (outx || outy) {
+                            out = true;
+                            const int oa = (int)((OPP_PACK >> (4 * h_a)) & 15u);
+                            v = StorageTraits<ST>::cvt(r0[oa * T::BWX + ch]) +
+                                bb_term(h_a, h_ex, h_ey, sx, sy, outx, outy);
+                        }
+                    }
+                    if (!out) v = StorageTraits<ST>::cvt(src[h_a * T::BWX + ch - h_ex]);
+                }
+                v += __shfl_xor_sync(FULL, v, 8);
+                v += __shfl_xor_sync(FULL, v, 4);
+                v += __shfl_xor_sync(FULL, v, 2);
+                v += __shfl_xor_sync(FULL, v, 1);
+                const R sl = __shfl_sync(FULL, v, 0), sr = __shfl_sync(FULL, v, 16);
+                rho_l = need_l ? R(1) + sl : R(-1);
+                rho_r = need_r ? R(1) + sr : R(-1);
                 return;
             }
             const bool row_in = p.pery || (r >= 0 && r < p.ny);
