@@ -84,6 +84,7 @@ struct lbm_ctx {
     double *d_snap_ux = nullptr, *d_snap_uy = nullptr, *d_partials = nullptr, *d_result = nullptr;
     unsigned long long *d_guard = nullptr;
     int *d_err = nullptr;        // set by a step kernel whose bounded wait expired
+    unsigned int *d_work = nullptr;  // step-kernel work counters (zero between launches)
     CUtensorMap tload[2];        // TMA load descriptors of f[0], f[1]
     CUtensorMap tstore[2];       // TMA store descriptors of f[0], f[1]
     double *h_result = nullptr;  // pinned, 5 doubles
@@ -127,6 +128,7 @@ StepParams make_params(const lbm_ctx *c)
     p.solid = c->d_solid;
     p.guard_count = c->d_guard;
     p.error = c->d_err;
+    p.work = c->d_work;
     p.cf.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
     p.cd.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
     p.nstrips = (c->nx + WS - 1) / WS;
@@ -140,11 +142,13 @@ StepParams make_params(const lbm_ctx *c)
     const int resident = c->num_sms * bps * WARPS;  // resident warps
     int Ly = c->Ly_option;
     if (Ly <= 0) {
-        // at most one item per resident warp (no partly filled second round);
-        // long segments keep the four halo source rows of each a small fraction
-        int nseg = resident / p.nstrips;
+        // about four items per resident warp (handed out dynamically), segments
+        // of at least 16 rows so the four halo source rows of each stay a small
+        // fraction of the reads
+        int nseg = (4 * resident + p.nstrips - 1) / p.nstrips;
         if (nseg < 1) nseg = 1;
         Ly = (c->ny + nseg - 1) / nseg;
+        if (Ly < 16) Ly = 16;
         if (Ly < 2) Ly = 2;
     }
     if (Ly > c->ny) Ly = c->ny;
@@ -199,6 +203,7 @@ lbm_status check_device_error(lbm_ctx *c)
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error flag");
     if (v) {
         cudaMemset(c->d_err, 0, sizeof(int));
+        cudaMemset(c->d_work, 0, 2 * sizeof(unsigned int));
         return fail(LBM_ERR_CUDA, "a step kernel's bounded wait for its staged rows expired");
     }
     return LBM_OK;
@@ -227,6 +232,7 @@ void free_ctx(lbm_ctx *c)
     dev_free(c->d_result);
     dev_free(c->d_guard);
     dev_free(c->d_err);
+    dev_free(c->d_work);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -319,8 +325,9 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const l
     c->d_result = (double *)dev_alloc(8 * sizeof(double));
     c->d_guard = (unsigned long long *)dev_alloc(sizeof(unsigned long long));
     c->d_err = (int *)dev_alloc(sizeof(int));
+    c->d_work = (unsigned int *)dev_alloc(2 * sizeof(unsigned int));
     if (!c->f[0] || !c->f[1] || !c->d_snap_ux || !c->d_snap_uy || !c->d_partials || !c->d_result || !c->d_guard ||
-        !c->d_err) {
+        !c->d_err || !c->d_work) {
         free_ctx(c);
         return fail(LBM_ERR_OOM, "device allocation failed");
     }
@@ -351,6 +358,7 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const l
     }
     e = cudaMemsetAsync(c->d_guard, 0, sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_work, 0, 2 * sizeof(unsigned int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, pop_bytes(c), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_snap_ux, 0, N * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_snap_uy, 0, N * sizeof(double), c->stream);

@@ -77,6 +77,7 @@ struct StepParams {
     const uint8_t *solid;    // optional mask [ny][pitch], 1 = solid
     unsigned long long *guard_count;  // device counter, may be null
     int *error;              // device flag: set when a bounded wait expires
+    unsigned int *work;      // device work counters {next item, warps done}, zero between launches
     // work decomposition: items = warp strips x segments, each segment Ly rows
     int Ly, nstrips, nitems;
     Consts<float> cf;

@@ -29,6 +29,9 @@
 // columns beyond a periodic x edge are patched from global memory when a row
 // lands.  Walls and solids use half-way bounce-back with the moving-wall term.
 //
+// Work items (strip, row segment) are handed out through a device counter, so
+// the load balances dynamically; the last warp of a launch resets it.
+//
 // Every mbarrier wait is bounded in time; on expiry the warp records an error
 // in p.error, waits (bounded) for its own copies in flight and returns.
 #pragma once
@@ -172,9 +175,14 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
     const int h_ex = h_a < 9 ? (int)((EX_PACK >> (2 * h_a)) & 3u) - 1 : 0;
     const int h_ey = h_a < 9 ? (int)((EY_PACK >> (2 * h_a)) & 3u) - 1 : 0;
 
-    const int gwarp = blockIdx.x * WARPS + warp;
-    const int nwarps = gridDim.x * WARPS;
-    for (int item = gwarp; item < p.nitems && !abort; item += nwarps) {
+    // items are handed out dynamically (one atomic per item), so warps that
+    // finish early take more work and the slowest warp bounds the tail
+    auto next_item = [&]() -> int {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(p.work, 1u);
+        return __shfl_sync(FULL, it, 0);
+    };
+    for (int item = next_item(); item < p.nitems && !abort; item = next_item()) {
         const int strip = item % p.nstrips;
         const int seg = item / p.nstrips;
         const int x0 = strip * WS;
@@ -498,7 +506,16 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
             if (!mbar_wait_bounded(bars_u32 + 8 * (q % T::NSLOT), (q / T::NSLOT) & 1u)) break;
         }
     }
-    if (lane == 0) bulk_wait_all();  // stores done before the stage memory goes away
+    if (lane == 0) {
+        bulk_wait_all();  // stores done before the stage memory goes away
+        // sign off; the last warp of the launch resets the counters for the next one
+        __threadfence();
+        const unsigned total = gridDim.x * WARPS;
+        if (atomicAdd(p.work + 1, 1u) == total - 1) {
+            atomicExch(p.work, 0u);
+            atomicExch(p.work + 1, 0u);
+        }
+    }
     __syncwarp();
 }
 
