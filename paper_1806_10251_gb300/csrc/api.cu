@@ -142,13 +142,13 @@ StepParams make_params(const lbm_ctx *c)
     const int resident = c->num_sms * bps * WARPS;  // resident warps
     int Ly = c->Ly_option;
     if (Ly <= 0) {
-        // about four items per resident warp (handed out dynamically), segments
-        // of at least 16 rows so the four halo source rows of each stay a small
-        // fraction of the reads
+        // at least four items per resident warp (handed out dynamically) and
+        // segments of at most 24 rows: short items keep the tail short, while
+        // each item re-reads four halo source rows and pulls one extra row
         int nseg = (4 * resident + p.nstrips - 1) / p.nstrips;
         if (nseg < 1) nseg = 1;
         Ly = (c->ny + nseg - 1) / nseg;
-        if (Ly < 16) Ly = 16;
+        if (Ly > 24) Ly = 24;
         if (Ly < 2) Ly = 2;
     }
     if (Ly > c->ny) Ly = c->ny;
