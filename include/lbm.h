@@ -156,6 +156,41 @@ lbm_status lbm_set_allocator(const lbm_allocator *a);
 /* Number of step-kernel launches made by this context so far. */
 lbm_status lbm_kernel_launches(lbm_ctx *ctx, long *launches);
 
+/* ---- Convergence sums without any device allocation -------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot let the library call cudaMalloc while they run: applications whose
+ * device memory is all handed out by their own pool or arena, loops that must
+ * not pay or risk an allocation between steps, and code recorded into a CUDA
+ * graph, where an allocation call cannot be recorded.  The caller passes its
+ * own device buffers; the reduction's scratch is a fixed array inside the
+ * library (2.5 MiB on every GPU that loads the library, held until exit).
+ *
+ * Computes, over the fluid cells of the population array f_dev (device,
+ * layout [9][ny][pitch], deviations f - w of the given storage type), the same
+ * five FP64 sums as lbm_residual: {sum |u - u_snap|^2, sum |u|^2, sum rho,
+ * sum rho ux, sum rho uy}, with rho u = sum f e - F/(2 gamma); then replaces
+ * the snapshot snap_ux_dev / snap_uy_dev (device, nx*ny doubles, index
+ * y*nx + x) by u.  sums_dev (device, 5 doubles) receives the sums.  Work is
+ * queued on `stream` (a cudaStream_t; NULL = the default stream) and nothing
+ * is allocated, freed or synchronised.
+ *
+ * The first call on a device looks up the scratch array's device address for
+ * that device; make it before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU race, so order them (e.g. one stream).
+ * nx*ny above LBM_NOALLOC_MAX_CELLS gives LBM_ERR_INVALID. */
+#define LBM_NOALLOC_MAX_PARTIALS 65536
+#define LBM_NOALLOC_MAX_CELLS (65536LL * 256LL)
+typedef struct {
+    int nx, ny;                /* cells                                           */
+    int pitch;                 /* row stride of each plane in elements, >= nx      */
+    int storage;               /* LBM_STORAGE_* element type of f_dev              */
+    double gamma;              /* preconditioning parameter                        */
+    double fx, fy;             /* uniform body force (0 if none)                   */
+    const uint8_t *solid_dev;  /* optional device mask [ny][pitch], non-zero solid */
+} lbm_population_desc;
+lbm_status lbm_residual_sums_noalloc(const lbm_population_desc *desc, const void *f_dev, double *snap_ux_dev,
+                                     double *snap_uy_dev, double *sums_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

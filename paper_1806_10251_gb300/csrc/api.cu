@@ -23,6 +23,12 @@ lbm_status fail(lbm_status s, const std::string &msg)
     return s;
 }
 
+}  // namespace
+
+lbm_status lbm::set_error(lbm_status s, const std::string &msg) { return fail(s, msg); }
+
+namespace {
+
 lbm_status cuda_fail(cudaError_t e, const char *where)
 {
     return fail(LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));

@@ -118,4 +118,7 @@ cudaError_t launch_pops_from_f64(const StepParams &p, int storage, const double 
 
 size_t storage_bytes(int storage);
 
+// Record a message for lbm_last_error() on this thread and return the status.
+lbm_status set_error(lbm_status s, const std::string &msg);
+
 }  // namespace lbm

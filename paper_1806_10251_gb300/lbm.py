@@ -39,6 +39,15 @@ class Boundaries(ctypes.Structure):
                 ("solid", ctypes.c_void_p)]
 
 
+class PopulationDesc(ctypes.Structure):
+    """lbm_population_desc: a caller-owned device population array."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_int), ("storage", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("solid_dev", ctypes.c_void_p)]
+
+
+NOALLOC_MAX_CELLS = 65536 * 256
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -77,6 +86,7 @@ SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_set_allocator": (ctypes.c_int, [ctypes.POINTER(Allocator)]),
     "lbm_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(_L)]),
+    "lbm_residual_sums_noalloc": (ctypes.c_int, [ctypes.POINTER(PopulationDesc), _P, _P, _P, _P, _P]),
 }
 
 
@@ -281,6 +291,14 @@ class Solver:
 
     def load(self, path: str):
         check(lib().lbm_load(self._h, os.fspath(path).encode()))
+
+
+def residual_sums_noalloc(desc: PopulationDesc, f_dev: int, snap_ux_dev: int, snap_uy_dev: int, sums_dev: int,
+                          stream: Optional[int] = None) -> None:
+    """lbm_residual_sums_noalloc on caller-owned device buffers (raw pointers)."""
+    check(lib().lbm_residual_sums_noalloc(ctypes.byref(desc), ctypes.c_void_p(f_dev), ctypes.c_void_p(snap_ux_dev),
+                                          ctypes.c_void_p(snap_uy_dev), ctypes.c_void_p(sums_dev),
+                                          ctypes.c_void_p(stream) if stream else None))
 
 
 def solver_from_case(case, gi_mode: int = GI_FULL, storage: int = STORAGE_F32, **options) -> Solver:
