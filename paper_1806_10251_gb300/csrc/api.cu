@@ -61,15 +61,6 @@ void dev_free(void *p)
     else cudaFree(p);
 }
 
-// RAII holder for temporary device buffers.
-struct DevBuf {
-    void *p = nullptr;
-    explicit DevBuf(size_t bytes) : p(dev_alloc(bytes)) {}
-    ~DevBuf() { dev_free(p); }
-    DevBuf(const DevBuf &) = delete;
-    DevBuf &operator=(const DevBuf &) = delete;
-};
-
 }  // namespace
 
 struct lbm_ctx {
@@ -94,6 +85,8 @@ struct lbm_ctx {
     CUtensorMap tload[2];        // TMA load descriptors of f[0], f[1]
     CUtensorMap tstore[2];       // TMA store descriptors of f[0], f[1]
     double *h_result = nullptr;  // pinned, 5 doubles
+    void *d_stage = nullptr;     // grow-only device staging for field and population transfers
+    size_t stage_bytes = 0;
     int res_blocks = 1;
     cudaStream_t own_stream = nullptr, stream = nullptr;
     long steps = 0, launches = 0;
@@ -239,9 +232,23 @@ void free_ctx(lbm_ctx *c)
     dev_free(c->d_guard);
     dev_free(c->d_err);
     dev_free(c->d_work);
+    dev_free(c->d_stage);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
+}
+
+// Device staging buffer of at least `bytes` (kept for the context's lifetime).
+void *stage_buffer(lbm_ctx *c, size_t bytes)
+{
+    if (bytes <= c->stage_bytes) return c->d_stage;
+    if (c->d_stage) {
+        cudaStreamSynchronize(c->stream);
+        dev_free(c->d_stage);
+    }
+    c->d_stage = dev_alloc(bytes);
+    c->stage_bytes = c->d_stage ? bytes : 0;
+    return c->d_stage;
 }
 
 lbm_status snapshot_reset(lbm_ctx *c)
@@ -509,14 +516,15 @@ lbm_status lbm_init_fields(lbm_ctx *c, const double *rho, const double *ux, cons
     if (check_ctx(c)) return LBM_ERR_INVALID;
     const size_t N = (size_t)c->nx * c->ny;
     const double *src[3] = {rho, ux, uy};
-    DevBuf b0(rho ? N * 8 : 0), b1(ux ? N * 8 : 0), b2(uy ? N * 8 : 0);
-    DevBuf *bufs[3] = {&b0, &b1, &b2};
     const double *dptr[3] = {nullptr, nullptr, nullptr};
-    for (int i = 0; i < 3; ++i) {
-        if (!src[i]) continue;
-        if (!bufs[i]->p) return fail(LBM_ERR_OOM, "device allocation failed (init)");
-        LBM_CUDA(cudaMemcpyAsync(bufs[i]->p, src[i], N * 8, cudaMemcpyHostToDevice, c->stream));
-        dptr[i] = (const double *)bufs[i]->p;
+    if (rho || ux || uy) {
+        double *stage = (double *)stage_buffer(c, 3 * N * sizeof(double));
+        if (!stage) return fail(LBM_ERR_OOM, "device allocation failed (init staging)");
+        for (int i = 0; i < 3; ++i) {
+            if (!src[i]) continue;
+            LBM_CUDA(cudaMemcpyAsync(stage + i * N, src[i], N * 8, cudaMemcpyHostToDevice, c->stream));
+            dptr[i] = stage + i * N;
+        }
     }
     StepParams p = make_params(c);
     LBM_CUDA(launch_init_eq(p, c->storage, dptr[0], dptr[1], dptr[2], c->f[c->cur], c->stream));
@@ -615,18 +623,15 @@ lbm_status lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy)
 {
     if (check_ctx(c)) return LBM_ERR_INVALID;
     const size_t N = (size_t)c->nx * c->ny;
-    DevBuf b(3 * N * sizeof(double));
-    if (!b.p) return fail(LBM_ERR_OOM, "device allocation failed (fields)");
-    double *d = (double *)b.p;
+    double *d = (double *)stage_buffer(c, 3 * N * sizeof(double));
+    if (!d) return fail(LBM_ERR_OOM, "device allocation failed (fields staging)");
     StepParams p = make_params(c);
     LBM_CUDA(launch_fields(p, c->storage, c->f[c->cur], d, d + N, d + 2 * N, c->stream));
+    if (rho) LBM_CUDA(cudaMemcpyAsync(rho, d, N * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (ux) LBM_CUDA(cudaMemcpyAsync(ux, d + N, N * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (uy) LBM_CUDA(cudaMemcpyAsync(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
-    lbm_status s = check_device_error(c);
-    if (s != LBM_OK) return s;
-    if (rho) LBM_CUDA(cudaMemcpy(rho, d, N * 8, cudaMemcpyDeviceToHost));
-    if (ux) LBM_CUDA(cudaMemcpy(ux, d + N, N * 8, cudaMemcpyDeviceToHost));
-    if (uy) LBM_CUDA(cudaMemcpy(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost));
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 lbm_status lbm_get_populations(lbm_ctx *c, double *f)
@@ -634,15 +639,13 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
     if (check_ctx(c)) return LBM_ERR_INVALID;
     if (!f) return fail(LBM_ERR_INVALID, "null output");
     const size_t N = (size_t)c->nx * c->ny;
-    DevBuf b(9 * N * sizeof(double));
-    if (!b.p) return fail(LBM_ERR_OOM, "device allocation failed (populations)");
+    double *d = (double *)stage_buffer(c, 9 * N * sizeof(double));
+    if (!d) return fail(LBM_ERR_OOM, "device allocation failed (population staging)");
     StepParams p = make_params(c);
-    LBM_CUDA(launch_pops_to_f64(p, c->storage, c->f[c->cur], (double *)b.p, c->stream));
+    LBM_CUDA(launch_pops_to_f64(p, c->storage, c->f[c->cur], d, c->stream));
+    LBM_CUDA(cudaMemcpyAsync(f, d, 9 * N * 8, cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
-    lbm_status s = check_device_error(c);
-    if (s != LBM_OK) return s;
-    LBM_CUDA(cudaMemcpy(f, b.p, 9 * N * 8, cudaMemcpyDeviceToHost));
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
@@ -650,12 +653,11 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
     if (check_ctx(c)) return LBM_ERR_INVALID;
     if (!f) return fail(LBM_ERR_INVALID, "null input");
     const size_t N = (size_t)c->nx * c->ny;
-    DevBuf b(9 * N * sizeof(double));
-    if (!b.p) return fail(LBM_ERR_OOM, "device allocation failed (populations)");
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
-    LBM_CUDA(cudaMemcpy(b.p, f, 9 * N * 8, cudaMemcpyHostToDevice));
+    double *d = (double *)stage_buffer(c, 9 * N * sizeof(double));
+    if (!d) return fail(LBM_ERR_OOM, "device allocation failed (population staging)");
+    LBM_CUDA(cudaMemcpyAsync(d, f, 9 * N * 8, cudaMemcpyHostToDevice, c->stream));
     StepParams p = make_params(c);
-    LBM_CUDA(launch_pops_from_f64(p, c->storage, (const double *)b.p, c->f[c->cur], c->stream));
+    LBM_CUDA(launch_pops_from_f64(p, c->storage, d, c->f[c->cur], c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }

@@ -2,6 +2,8 @@
 // convergence residual, and population format conversions.
 #include <math.h>
 
+#include <type_traits>
+
 #include "d2q9_collide.cuh"
 
 namespace lbm {
@@ -16,24 +18,54 @@ size_t storage_bytes(int storage)
     }
 }
 
-// Generic element access in FP64 for the one-off kernels below.
+// Element access in FP64 by storage type (compile time for the per-step
+// kernels, run time for the one-off format conversions).
+template <typename ST> __device__ __forceinline__ double ld64(const ST *f, size_t i);
+template <> __device__ __forceinline__ double ld64<float>(const float *f, size_t i) { return (double)f[i]; }
+template <> __device__ __forceinline__ double ld64<double>(const double *f, size_t i) { return f[i]; }
+template <> __device__ __forceinline__ double ld64<__half>(const __half *f, size_t i) { return (double)__half2float(f[i]); }
+template <> __device__ __forceinline__ double ld64<__nv_bfloat16>(const __nv_bfloat16 *f, size_t i)
+{
+    return (double)__bfloat162float(f[i]);
+}
+template <typename ST> __device__ __forceinline__ void st64(ST *f, size_t i, double v);
+template <> __device__ __forceinline__ void st64<float>(float *f, size_t i, double v) { f[i] = (float)v; }
+template <> __device__ __forceinline__ void st64<double>(double *f, size_t i, double v) { f[i] = v; }
+template <> __device__ __forceinline__ void st64<__half>(__half *f, size_t i, double v) { f[i] = __double2half(v); }
+template <> __device__ __forceinline__ void st64<__nv_bfloat16>(__nv_bfloat16 *f, size_t i, double v)
+{
+    f[i] = __double2bfloat16(v);
+}
+
 __device__ __forceinline__ double load_any(const void *f, int storage, size_t i)
 {
     switch (storage) {
-    case LBM_STORAGE_F16: return (double)__half2float(static_cast<const __half *>(f)[i]);
-    case LBM_STORAGE_BF16: return (double)__bfloat162float(static_cast<const __nv_bfloat16 *>(f)[i]);
-    case LBM_STORAGE_F64: return static_cast<const double *>(f)[i];
-    default: return (double)static_cast<const float *>(f)[i];
+    case LBM_STORAGE_F16: return ld64(static_cast<const __half *>(f), i);
+    case LBM_STORAGE_BF16: return ld64(static_cast<const __nv_bfloat16 *>(f), i);
+    case LBM_STORAGE_F64: return ld64(static_cast<const double *>(f), i);
+    default: return ld64(static_cast<const float *>(f), i);
     }
 }
 
 __device__ __forceinline__ void store_any(void *f, int storage, size_t i, double v)
 {
     switch (storage) {
-    case LBM_STORAGE_F16: static_cast<__half *>(f)[i] = __double2half(v); break;
-    case LBM_STORAGE_BF16: static_cast<__nv_bfloat16 *>(f)[i] = __double2bfloat16(v); break;
-    case LBM_STORAGE_F64: static_cast<double *>(f)[i] = v; break;
-    default: static_cast<float *>(f)[i] = (float)v; break;
+    case LBM_STORAGE_F16: st64(static_cast<__half *>(f), i, v); break;
+    case LBM_STORAGE_BF16: st64(static_cast<__nv_bfloat16 *>(f), i, v); break;
+    case LBM_STORAGE_F64: st64(static_cast<double *>(f), i, v); break;
+    default: st64(static_cast<float *>(f), i, v); break;
+    }
+}
+
+// Call fn(ST *) with the population pointer cast to the storage type.
+template <typename F>
+void with_storage(int storage, const void *f, F &&fn)
+{
+    switch (storage) {
+    case LBM_STORAGE_F16: fn(static_cast<const __half *>(f)); break;
+    case LBM_STORAGE_BF16: fn(static_cast<const __nv_bfloat16 *>(f)); break;
+    case LBM_STORAGE_F64: fn(static_cast<const double *>(f)); break;
+    default: fn(static_cast<const float *>(f)); break;
     }
 }
 
@@ -71,9 +103,10 @@ __device__ __forceinline__ void pops_from_raw(const double (&k)[9], double (&f)[
 
 // f~0 = f_eq(rho, u) - S/2 stored as deviations from w (rho0 = 1).  Raw
 // equilibria of Eq. 15 with the gamma^2 cubic terms; the fourth moment makes
-// the central fourth moment rho/9.
-__global__ void init_eq_kernel(const StepParams p, int storage, const double *rho_in,
-                               const double *ux_in, const double *uy_in, void *f)
+// the central fourth moment rho/9.  ig = 1/gamma, ig2 = 1/gamma^2.
+template <typename ST>
+__global__ void init_eq_kernel(const StepParams p, const double *rho_in, const double *ux_in, const double *uy_in,
+                               ST *f, double ig, double ig2)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -82,64 +115,69 @@ __global__ void init_eq_kernel(const StepParams p, int storage, const double *rh
     const double r = rho_in ? rho_in[ic] : 1.0;
     const double u = ux_in ? ux_in[ic] : 0.0;
     const double v = uy_in ? uy_in[ic] : 0.0;
-    const double g = p.gamma;
+    const double third = 1.0 / 3.0;
     double k[9] = {r,
                    r * u,
                    r * v,
-                   r / 3.0 + r * u * u / g,
-                   r / 3.0 + r * v * v / g,
-                   r * u * v / g,
-                   r * v / 3.0 + r * u * u * v / (g * g),
-                   r * u / 3.0 + r * u * v * v / (g * g),
-                   r / 9.0 + r * (u * u + v * v) / 3.0 + r * u * u * v * v * (3.0 - 6.0 / g + 4.0 / (g * g))};
+                   r * third + r * u * u * ig,
+                   r * third + r * v * v * ig,
+                   r * u * v * ig,
+                   r * v * third + r * u * u * v * ig2,
+                   r * u * third + r * u * v * v * ig2,
+                   r * (1.0 / 9.0) + r * (u * u + v * v) * third + r * u * u * v * v * (3.0 - 6.0 * ig + 4.0 * ig2)};
     double feq[9], S[9];
     pops_from_raw(k, feq);
     double Fx, Fy;
     force_at(p, x, y, Fx, Fy);
     double s[9] = {0.0,
-                   Fx / g,
-                   Fy / g,
-                   2.0 * Fx * u / (g * g),
-                   2.0 * Fy * v / (g * g),
-                   (Fx * v + Fy * u) / (g * g),
+                   Fx * ig,
+                   Fy * ig,
+                   2.0 * Fx * u * ig2,
+                   2.0 * Fy * v * ig2,
+                   (Fx * v + Fy * u) * ig2,
                    Fy * u * u + 2.0 * Fx * u * v,
                    Fx * v * v + 2.0 * Fy * v * u,
                    2.0 * (Fx * u * v * v + Fy * v * u * u)};
     pops_from_raw(s, S);
     const size_t i = (size_t)y * p.pitch + x;
-    for (int a = 0; a < 9; ++a)
-        store_any(f, storage, (size_t)a * p.plane + i, feq[a] - weight(a) - 0.5 * S[a]);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) st64(f, (size_t)a * p.plane + i, feq[a] - weight(a) - 0.5 * S[a]);
 }
 
 cudaError_t launch_init_eq(const StepParams &p, int storage, const double *rho, const double *ux,
                            const double *uy, void *f, cudaStream_t s)
 {
     dim3 grid((p.nx + 127) / 128, p.ny);
-    init_eq_kernel<<<grid, 128, 0, s>>>(p, storage, rho, ux, uy, f);
+    const double ig = 1.0 / p.gamma, ig2 = ig * ig;
+    with_storage(storage, f, [&](auto *fp) {
+        using ST = std::remove_const_t<std::remove_pointer_t<decltype(fp)>>;
+        init_eq_kernel<ST><<<grid, 128, 0, s>>>(p, rho, ux, uy, const_cast<ST *>(fp), ig, ig2);
+    });
     return cudaGetLastError();
 }
 
 // Observed fields: rho = 1 + sum g~, rho u = sum g~ e - F/(2 gamma); NaN in solids.
-__device__ __forceinline__ void local_fields(const StepParams &p, int storage, const void *f, int x,
-                                             int y, double &rho, double &ux, double &uy)
+template <typename ST>
+__device__ __forceinline__ void local_fields(const StepParams &p, const ST *f, int x, int y, double half_ig, double &rho,
+                                             double &ux, double &uy)
 {
     const size_t i = (size_t)y * p.pitch + x;
-    double s = 0.0, jx = 0.0, jy = 0.0;
-    for (int a = 0; a < 9; ++a) {
-        const double ga = load_any(f, storage, (size_t)a * p.plane + i);
-        s += ga;
-        jx += ga * cx(a);
-        jy += ga * cy(a);
-    }
+    double g[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) g[a] = ld64(f, (size_t)a * p.plane + i);
+    const double s = g[0] + (g[1] + g[3]) + (g[2] + g[4]) + ((g[5] + g[6]) + (g[7] + g[8]));
+    const double jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const double jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
     double Fx, Fy;
     force_at(p, x, y, Fx, Fy);
     rho = 1.0 + s;
-    ux = (jx - 0.5 * Fx / p.gamma) / rho;
-    uy = (jy - 0.5 * Fy / p.gamma) / rho;
+    const double irho = __drcp_rn(rho);
+    ux = (jx - Fx * half_ig) * irho;
+    uy = (jy - Fy * half_ig) * irho;
 }
 
-__global__ void fields_kernel(const StepParams p, int storage, const void *f, double *rho, double *ux,
-                              double *uy)
+template <typename ST>
+__global__ void fields_kernel(const StepParams p, const ST *f, double half_ig, double *rho, double *ux, double *uy)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -149,7 +187,7 @@ __global__ void fields_kernel(const StepParams p, int storage, const void *f, do
     if (solid_at(p, x, y)) {
         r = u = v = nan("");
     } else {
-        local_fields(p, storage, f, x, y, r, u, v);
+        local_fields(p, f, x, y, half_ig, r, u, v);
     }
     if (rho) rho[o] = r;
     if (ux) ux[o] = u;
@@ -160,15 +198,20 @@ cudaError_t launch_fields(const StepParams &p, int storage, const void *f, doubl
                           double *uy, cudaStream_t s)
 {
     dim3 grid((p.nx + 127) / 128, p.ny);
-    fields_kernel<<<grid, 128, 0, s>>>(p, storage, f, rho, ux, uy);
+    const double half_ig = 0.5 / p.gamma;
+    with_storage(storage, f, [&](auto *fp) {
+        using ST = std::remove_const_t<std::remove_pointer_t<decltype(fp)>>;
+        fields_kernel<ST><<<grid, 128, 0, s>>>(p, fp, half_ig, rho, ux, uy);
+    });
     return cudaGetLastError();
 }
 
 // ---- FP64 convergence residual ------------------------------------------------
 // Pass 1: each block accumulates {sum|du|^2, sum|u|^2, sum rho, sum rho ux,
-// sum rho uy} over a grid-stride range of fluid cells, reduces in FP64 with warp
-// shuffles and writes one row of `partials`; the velocity snapshot is replaced.
-// Pass 2: one block reduces the rows in a fixed order (deterministic).
+// sum rho uy} over whole rows of fluid cells (rows blockIdx.x, + gridDim.x,
+// ...), reduces in FP64 with warp shuffles and writes one row of `partials`;
+// the velocity snapshot is replaced.  Pass 2: one block reduces the rows in a
+// fixed order (deterministic).
 constexpr int RES_THREADS = 256;
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -198,24 +241,26 @@ __device__ __forceinline__ void block_sum5(double (&v)[5], double *out)
     }
 }
 
-__global__ void residual_pass1(const StepParams p, int storage, const void *f, double *snap_ux,
-                               double *snap_uy, double *partials)
+template <typename ST>
+__global__ void residual_pass1(const StepParams p, const ST *f, double half_ig, double *snap_ux, double *snap_uy,
+                               double *partials)
 {
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    const size_t N = (size_t)p.nx * p.ny;
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(c % p.nx), y = (int)(c / p.nx);
-        if (solid_at(p, x, y)) continue;
-        double r, u, v;
-        local_fields(p, storage, f, x, y, r, u, v);
-        const double du = u - snap_ux[c], dv = v - snap_uy[c];
-        acc[0] += du * du + dv * dv;
-        acc[1] += u * u + v * v;
-        acc[2] += r;
-        acc[3] += r * u;
-        acc[4] += r * v;
-        snap_ux[c] = u;
-        snap_uy[c] = v;
+    for (int y = blockIdx.x; y < p.ny; y += gridDim.x) {
+        for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
+            if (solid_at(p, x, y)) continue;
+            const size_t c = (size_t)y * p.nx + x;
+            double r, u, v;
+            local_fields(p, f, x, y, half_ig, r, u, v);
+            const double du = u - snap_ux[c], dv = v - snap_uy[c];
+            acc[0] += du * du + dv * dv;
+            acc[1] += u * u + v * v;
+            acc[2] += r;
+            acc[3] += r * u;
+            acc[4] += r * v;
+            snap_ux[c] = u;
+            snap_uy[c] = v;
+        }
     }
     block_sum5<RES_THREADS>(acc, partials + (size_t)blockIdx.x * 5);
 }
@@ -230,16 +275,19 @@ __global__ void residual_pass2(const double *partials, int nrows, double *result
 
 int residual_blocks(const StepParams &p)
 {
-    const size_t N = (size_t)p.nx * p.ny;
-    size_t b = (N + RES_THREADS - 1) / RES_THREADS;
-    return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+    // one block per row (each block walks rows with a stride), at most 1024
+    return p.ny < 1024 ? (p.ny < 1 ? 1 : p.ny) : 1024;
 }
 
 cudaError_t launch_residual(const StepParams &p, int storage, const void *f, double *snap_ux,
                             double *snap_uy, double *partials, int nblocks, double *result,
                             cudaStream_t s)
 {
-    residual_pass1<<<nblocks, RES_THREADS, 0, s>>>(p, storage, f, snap_ux, snap_uy, partials);
+    const double half_ig = 0.5 / p.gamma;
+    with_storage(storage, f, [&](auto *fp) {
+        using ST = std::remove_const_t<std::remove_pointer_t<decltype(fp)>>;
+        residual_pass1<ST><<<nblocks, RES_THREADS, 0, s>>>(p, fp, half_ig, snap_ux, snap_uy, partials);
+    });
     residual_pass2<<<1, RES_THREADS, 0, s>>>(partials, nblocks, result);
     return cudaGetLastError();
 }
