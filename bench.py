@@ -37,7 +37,7 @@ KERNEL_SOURCES = ["paper_1806_10251_gb300/csrc/stream_collide.cuh",
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=list(STORAGE_CODE), default="f32")
@@ -101,7 +101,7 @@ class ClockSampler:
         self.device_id = device_id
 
     def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
         if self.device_id:
             cmd += ["-i", self.device_id]
         try:

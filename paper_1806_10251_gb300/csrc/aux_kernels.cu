@@ -86,62 +86,74 @@ __device__ __forceinline__ void force_at(const StepParams &p, int x, int y, doub
     }
 }
 
+// Compute precision of the per-cell auxiliary work: FP32 for the 32- and
+// 16-bit formats (their stored values carry no more), FP64 for FP64 storage.
+template <typename ST> struct AuxReal { using R = float; };
+template <> struct AuxReal<double> { using R = double; };
+
 // Inverse of the Eq. 5 map for the moment order
-// (k0, kx, ky, kxx, kyy, kxy, kxxy, kxyy, kxxyy).
-__device__ __forceinline__ void pops_from_raw(const double (&k)[9], double (&f)[9])
+// (k0, kx, ky, kxx, kyy, kxy, kxxy, kxyy, kxxyy), in precision R.
+template <typename R>
+__device__ __forceinline__ void pops_from_raw_r(const R (&k)[9], R (&f)[9])
 {
     f[0] = k[0] - k[3] - k[4] + k[8];
-    f[1] = 0.5 * (k[1] + k[3] - k[7] - k[8]);
-    f[3] = 0.5 * (-k[1] + k[3] + k[7] - k[8]);
-    f[2] = 0.5 * (k[2] + k[4] - k[6] - k[8]);
-    f[4] = 0.5 * (-k[2] + k[4] + k[6] - k[8]);
-    f[5] = 0.25 * (k[5] + k[6] + k[7] + k[8]);
-    f[6] = 0.25 * (-k[5] + k[6] - k[7] + k[8]);
-    f[7] = 0.25 * (k[5] - k[6] - k[7] + k[8]);
-    f[8] = 0.25 * (-k[5] - k[6] + k[7] + k[8]);
+    f[1] = R(0.5) * (k[1] + k[3] - k[7] - k[8]);
+    f[3] = R(0.5) * (-k[1] + k[3] + k[7] - k[8]);
+    f[2] = R(0.5) * (k[2] + k[4] - k[6] - k[8]);
+    f[4] = R(0.5) * (-k[2] + k[4] + k[6] - k[8]);
+    f[5] = R(0.25) * (k[5] + k[6] + k[7] + k[8]);
+    f[6] = R(0.25) * (-k[5] + k[6] - k[7] + k[8]);
+    f[7] = R(0.25) * (k[5] - k[6] - k[7] + k[8]);
+    f[8] = R(0.25) * (-k[5] - k[6] + k[7] + k[8]);
 }
 
-// f~0 = f_eq(rho, u) - S/2 stored as deviations from w (rho0 = 1).  Raw
-// equilibria of Eq. 15 with the gamma^2 cubic terms; the fourth moment makes
-// the central fourth moment rho/9.  ig = 1/gamma, ig2 = 1/gamma^2.
+// f~0 = f_eq(rho, u) - S/2 stored as deviations g = f - w (rho0 = 1).  The
+// raw equilibria of Eq. 15 (gamma^2 cubic terms; fourth moment such that the
+// central fourth moment is rho/9) are written minus the rest-state moments
+// (1, 0, 0, 1/3, 1/3, 0, 0, 0, 1/9), so the inverse map yields g directly and
+// no O(1) weight is subtracted in finite precision.  ig = 1/gamma, ig2 = 1/gamma^2.
 template <typename ST>
 __global__ void init_eq_kernel(const StepParams p, const double *rho_in, const double *ux_in, const double *uy_in,
-                               ST *f, double ig, double ig2)
+                               ST *f, double ig_d, double ig2_d)
 {
+    using R = typename AuxReal<ST>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const size_t ic = (size_t)y * p.nx + x;
-    const double r = rho_in ? rho_in[ic] : 1.0;
-    const double u = ux_in ? ux_in[ic] : 0.0;
-    const double v = uy_in ? uy_in[ic] : 0.0;
-    const double third = 1.0 / 3.0;
-    double k[9] = {r,
-                   r * u,
-                   r * v,
-                   r * third + r * u * u * ig,
-                   r * third + r * v * v * ig,
-                   r * u * v * ig,
-                   r * v * third + r * u * u * v * ig2,
-                   r * u * third + r * u * v * v * ig2,
-                   r * (1.0 / 9.0) + r * (u * u + v * v) * third + r * u * u * v * v * (3.0 - 6.0 * ig + 4.0 * ig2)};
-    double feq[9], S[9];
-    pops_from_raw(k, feq);
-    double Fx, Fy;
-    force_at(p, x, y, Fx, Fy);
-    double s[9] = {0.0,
-                   Fx * ig,
-                   Fy * ig,
-                   2.0 * Fx * u * ig2,
-                   2.0 * Fy * v * ig2,
-                   (Fx * v + Fy * u) * ig2,
-                   Fy * u * u + 2.0 * Fx * u * v,
-                   Fx * v * v + 2.0 * Fy * v * u,
-                   2.0 * (Fx * u * v * v + Fy * v * u * u)};
-    pops_from_raw(s, S);
+    const R dr = rho_in ? R(rho_in[ic] - 1.0) : R(0);
+    const R r = R(1) + dr;
+    const R u = ux_in ? R(ux_in[ic]) : R(0);
+    const R v = uy_in ? R(uy_in[ic]) : R(0);
+    const R ig = R(ig_d), ig2 = R(ig2_d), third = R(1.0 / 3.0);
+    R k[9] = {dr,
+              r * u,
+              r * v,
+              dr * third + r * u * u * ig,
+              dr * third + r * v * v * ig,
+              r * u * v * ig,
+              r * v * third + r * u * u * v * ig2,
+              r * u * third + r * u * v * v * ig2,
+              dr * R(1.0 / 9.0) + r * (u * u + v * v) * third +
+                  r * u * u * v * v * (R(3) - R(6) * ig + R(4) * ig2)};
+    R geq[9], S[9];
+    pops_from_raw_r(k, geq);
+    double Fxd, Fyd;
+    force_at(p, x, y, Fxd, Fyd);
+    const R Fx = R(Fxd), Fy = R(Fyd);
+    R sm[9] = {R(0),
+               Fx * ig,
+               Fy * ig,
+               R(2) * Fx * u * ig2,
+               R(2) * Fy * v * ig2,
+               (Fx * v + Fy * u) * ig2,
+               Fy * u * u + R(2) * Fx * u * v,
+               Fx * v * v + R(2) * Fy * v * u,
+               R(2) * (Fx * u * v * v + Fy * v * u * u)};
+    pops_from_raw_r(sm, S);
     const size_t i = (size_t)y * p.pitch + x;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) st64(f, (size_t)a * p.plane + i, feq[a] - weight(a) - 0.5 * S[a]);
+    for (int a = 0; a < 9; ++a) st64(f, (size_t)a * p.plane + i, (double)(geq[a] - R(0.5) * S[a]));
 }
 
 cudaError_t launch_init_eq(const StepParams &p, int storage, const double *rho, const double *ux,
@@ -157,23 +169,34 @@ cudaError_t launch_init_eq(const StepParams &p, int storage, const double *rho, 
 }
 
 // Observed fields: rho = 1 + sum g~, rho u = sum g~ e - F/(2 gamma); NaN in solids.
+template <typename ST> __device__ __forceinline__ typename AuxReal<ST>::R ldr(const ST *f, size_t i)
+{
+    return (typename AuxReal<ST>::R)ld64(f, i);
+}
+__device__ __forceinline__ float recip_aux(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double recip_aux(double v) { return __drcp_rn(v); }
+
+// Observed fields of one cell in the compute precision of the storage type,
+// returned in FP64.
 template <typename ST>
 __device__ __forceinline__ void local_fields(const StepParams &p, const ST *f, int x, int y, double half_ig, double &rho,
                                              double &ux, double &uy)
 {
+    using R = typename AuxReal<ST>::R;
     const size_t i = (size_t)y * p.pitch + x;
-    double g[9];
+    R g[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) g[a] = ld64(f, (size_t)a * p.plane + i);
-    const double s = g[0] + (g[1] + g[3]) + (g[2] + g[4]) + ((g[5] + g[6]) + (g[7] + g[8]));
-    const double jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-    const double jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    for (int a = 0; a < 9; ++a) g[a] = ldr(f, (size_t)a * p.plane + i);
+    const R s = g[0] + (g[1] + g[3]) + (g[2] + g[4]) + ((g[5] + g[6]) + (g[7] + g[8]));
+    const R jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const R jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
     double Fx, Fy;
     force_at(p, x, y, Fx, Fy);
-    rho = 1.0 + s;
-    const double irho = __drcp_rn(rho);
-    ux = (jx - Fx * half_ig) * irho;
-    uy = (jy - Fy * half_ig) * irho;
+    const R r = R(1) + s;
+    const R ir = recip_aux(r);
+    rho = (double)r;
+    ux = (double)((jx - R(Fx * half_ig)) * ir);
+    uy = (double)((jy - R(Fy * half_ig)) * ir);
 }
 
 template <typename ST>
