@@ -93,7 +93,11 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U,
  *   "fx", "fy"  uniform body force (default 0)
  *   "guard"     1 = drop the velocity-dependent parts of the strain-rate solve
  *               where |D| < 0.1 |D0| (Eqs. 53-55; off by default), counted
- *   "cells_per_item" rows per work item of the step kernel (tuning; >= 1) */
+ *   "cells_per_item" rows per work item of the step kernel (tuning; >= 1)
+ *   "stochastic_rounding" FP16/BF16 storage: 1 (default) rounds each stored
+ *               deviation up or down with probability given by its distance
+ *               to the two neighbours (random bits: a hash of step, cell and
+ *               direction, so runs are reproducible); 0 rounds to nearest */
 lbm_status lbm_set_option(lbm_ctx *ctx, const char *key, double value);
 lbm_status lbm_get_option(lbm_ctx *ctx, const char *key, double *value);
 
@@ -155,6 +159,63 @@ lbm_status lbm_set_allocator(const lbm_allocator *a);
 
 /* Number of step-kernel launches made by this context so far. */
 lbm_status lbm_kernel_launches(lbm_ctx *ctx, long *launches);
+
+/* ---- Batches of steady solves and the serving loop ---------------------------
+ * A batch keeps many independent domains resident and advances all running
+ * ones together: one launch of the batched step kernel is one step (Eq. 2) of
+ * every running domain, the work list spanning all their (strip, row segment)
+ * items.  K steps (the check interval) are replayed from one captured CUDA
+ * graph; after each replay every running domain's convergence residual (as in
+ * lbm_run_to_steady) is checked in FP64, and converged, diverged or exhausted
+ * domains retire while the others go on (per-domain masking).  Requests wait in
+ * a FIFO queue and are admitted when their device footprint fits the batch's
+ * memory budget; finished requests keep their populations until released.
+ * Storage and collision kernel are per batch; the device memory of a batch is
+ * allocated with cudaMalloc.  A domain's results do not depend on the other
+ * domains in the batch.  submit/poll/fields/release may be called from any
+ * thread while the engine runs (lbm_batch_start) or between lbm_batch_run calls. */
+typedef struct lbm_batch lbm_batch;
+enum { LBM_REQ_QUEUED = 0, LBM_REQ_RUNNING = 1, LBM_REQ_CONVERGED = 2, LBM_REQ_NOT_CONVERGED = 3,
+       LBM_REQ_DIVERGED = 4, LBM_REQ_FAILED = 5 };
+typedef struct {
+    int nx, ny;              /* >= 3                                                 */
+    double nu, gamma, U;     /* as lbm_create                                        */
+    lbm_boundaries bnd;      /* sides and optional host solid mask (copied at submit) */
+    int use_bnd;             /* 0: lid-driven cavity with lid speed U                */
+    double fx, fy;           /* uniform body force                                   */
+    double tol;              /* steady when r < tol between checks (> 0)              */
+    long max_steps;          /* give up after this many steps (> 0)                  */
+} lbm_request;
+typedef struct {
+    int state;               /* LBM_REQ_*                                             */
+    long steps;              /* steps taken                                          */
+    double residual;         /* last convergence residual                            */
+    double t_submit, t_admit, t_done;  /* seconds since the batch was created        */
+} lbm_result;
+
+/* storage: LBM_STORAGE_*; gi_mode: LBM_GI_*; hbm_budget_bytes bounds the sum of
+ * the admitted requests' footprints (2 population buffers + residual snapshot
+ * + mask).  Options: "check_every" (K, even, default 1000: steps between
+ * convergence checks, one CUDA graph of K launches), "rows_per_item" (0 =
+ * autotune on the first admitted set), "stochastic_rounding" (as lbm_set_option,
+ * default 1, for domains admitted afterwards).  The error status of create is
+ * LBM_ERR_INVALID for bad arguments, LBM_ERR_CUDA without a device, LBM_ERR_OOM
+ * when the batch's own tables cannot be allocated.  A request is initialised at
+ * rest (rho = 1, u = 0); its step count includes autotuning steps. */
+lbm_status lbm_batch_create(size_t hbm_budget_bytes, int storage, int gi_mode, lbm_batch **out);
+lbm_status lbm_batch_set_option(lbm_batch *b, const char *key, double value);
+lbm_status lbm_batch_submit(lbm_batch *b, const lbm_request *req, long *id);   /* non-blocking */
+lbm_status lbm_batch_poll(lbm_batch *b, long id, int *done, lbm_result *res);  /* done: finished */
+lbm_status lbm_batch_fields(lbm_batch *b, long id, double *rho, double *ux, double *uy);
+lbm_status lbm_batch_release(lbm_batch *b, long id);  /* frees a finished request's memory */
+/* Run engine ticks on the calling thread until nothing is queued or running,
+ * or wall_seconds (> 0) have passed. */
+lbm_status lbm_batch_run(lbm_batch *b, double wall_seconds);
+lbm_status lbm_batch_start(lbm_batch *b);  /* engine on a background thread */
+lbm_status lbm_batch_stop(lbm_batch *b);
+/* stats: {cell updates, step launches, ticks, running, queued, device bytes in use} */
+lbm_status lbm_batch_stats(lbm_batch *b, double stats[6]);
+void lbm_batch_destroy(lbm_batch *b);
 
 /* ---- Convergence sums without any device allocation -------------------------
  * The paper has no counterpart to this entry point.  It is for callers that

@@ -71,6 +71,7 @@ struct lbm_ctx {
     int gi_mode = LBM_GI_FULL;
     int storage = LBM_STORAGE_F32;
     int guard = 0;
+    int sround = 1;  // 16-bit storage: stochastic rounding of the stored deviations
     lbm_side sides[4];
     double Fx = 0, Fy = 0;
     int Ly_option = 0;  // 0 = automatic
@@ -109,6 +110,8 @@ StepParams make_params(const lbm_ctx *c)
     p.pery = c->sides[2].kind == LBM_SIDE_PERIODIC;
     p.gi_mode = c->gi_mode;
     p.guard = c->guard;
+    p.sround = c->sround;
+    p.step = (unsigned int)c->steps;
     p.gamma = c->gamma;
     p.w3 = c->omega[3];
     p.w4 = c->omega[4];
@@ -420,6 +423,8 @@ lbm_status lbm_set_option(lbm_ctx *c, const char *key, double v)
         c->gi_mode = (int)v;
     } else if (k == "guard") {
         c->guard = v != 0.0;
+    } else if (k == "stochastic_rounding") {
+        c->sround = v != 0.0;
     } else if (k == "fx" || k == "fy") {
         if (!isfinite(v)) return fail(LBM_ERR_INVALID, "force must be finite");
         (k == "fx" ? c->Fx : c->Fy) = v;
@@ -471,6 +476,7 @@ lbm_status lbm_get_option(lbm_ctx *c, const char *key, double *v)
     if (k.size() == 6 && k.compare(0, 5, "omega") == 0 && k[5] >= '3' && k[5] <= '8') *v = c->omega[k[5] - '0'];
     else if (k == "gi_mode") *v = c->gi_mode;
     else if (k == "guard") *v = c->guard;
+    else if (k == "stochastic_rounding") *v = c->sround;
     else if (k == "fx") *v = c->Fx;
     else if (k == "fy") *v = c->Fy;
     else if (k == "storage") *v = c->storage;
@@ -543,6 +549,7 @@ lbm_status lbm_step(lbm_ctx *c, long n)
     StepParams p = make_params(c);
     const int grid = step_grid(c, p);
     for (long i = 0; i < n; ++i) {
+        p.step = (unsigned int)c->steps;  // seeds the stochastic rounding of 16-bit storage
         cudaError_t e = launch_step(c, p, grid);
         if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
         c->cur = 1 - c->cur;

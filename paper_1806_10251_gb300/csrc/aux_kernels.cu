@@ -23,7 +23,10 @@ size_t storage_bytes(int storage)
 template <typename ST> __device__ __forceinline__ double ld64(const ST *f, size_t i);
 template <> __device__ __forceinline__ double ld64<float>(const float *f, size_t i) { return (double)f[i]; }
 template <> __device__ __forceinline__ double ld64<double>(const double *f, size_t i) { return f[i]; }
-template <> __device__ __forceinline__ double ld64<__half>(const __half *f, size_t i) { return (double)__half2float(f[i]); }
+template <> __device__ __forceinline__ double ld64<__half>(const __half *f, size_t i)
+{
+    return (double)__half2float(f[i]) * (double)F16_INV_SCALE;
+}
 template <> __device__ __forceinline__ double ld64<__nv_bfloat16>(const __nv_bfloat16 *f, size_t i)
 {
     return (double)__bfloat162float(f[i]);
@@ -31,7 +34,10 @@ template <> __device__ __forceinline__ double ld64<__nv_bfloat16>(const __nv_bfl
 template <typename ST> __device__ __forceinline__ void st64(ST *f, size_t i, double v);
 template <> __device__ __forceinline__ void st64<float>(float *f, size_t i, double v) { f[i] = (float)v; }
 template <> __device__ __forceinline__ void st64<double>(double *f, size_t i, double v) { f[i] = v; }
-template <> __device__ __forceinline__ void st64<__half>(__half *f, size_t i, double v) { f[i] = __double2half(v); }
+template <> __device__ __forceinline__ void st64<__half>(__half *f, size_t i, double v)
+{
+    f[i] = __double2half(v * (double)F16_SCALE);
+}
 template <> __device__ __forceinline__ void st64<__nv_bfloat16>(__nv_bfloat16 *f, size_t i, double v)
 {
     f[i] = __double2bfloat16(v);

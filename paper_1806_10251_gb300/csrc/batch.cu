@@ -1,0 +1,798 @@
+// Batches of steady solves and the serving loop (continuous batching).
+//
+// A batch owns up to max_slots resident domains.  Every engine tick admits
+// queued requests whose device footprint fits the budget (FIFO), advances all
+// running domains K steps by replaying one captured CUDA graph of K launches
+// of the batched step kernel (all domains in lockstep), then checks each
+// running domain's FP64 convergence residual and retires the converged,
+// diverged and exhausted ones.  Per-domain tables (parameters, TMA
+// descriptors, active list, item prefix sums, active count) live in device
+// memory, so the graph stays valid while domains join and retire.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+cudaError_t launch_batch_f32(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_batch_f16(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_batch_bf16(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_batch_f64(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
+int batch_blocks_f32(int gi_mode);
+int batch_blocks_f16(int gi_mode);
+int batch_blocks_bf16(int gi_mode);
+int batch_blocks_f64(int gi_mode);
+
+cudaError_t launch_batch_step(int storage, int gi_mode, const BatchArgs &a, int grid, cudaStream_t s)
+{
+    switch (storage) {
+    case LBM_STORAGE_F16: return launch_batch_f16(gi_mode, a, grid, s);
+    case LBM_STORAGE_BF16: return launch_batch_bf16(gi_mode, a, grid, s);
+    case LBM_STORAGE_F64: return launch_batch_f64(gi_mode, a, grid, s);
+    default: return launch_batch_f32(gi_mode, a, grid, s);
+    }
+}
+
+int batch_blocks_per_sm(int storage, int gi_mode)
+{
+    switch (storage) {
+    case LBM_STORAGE_F16: return batch_blocks_f16(gi_mode);
+    case LBM_STORAGE_BF16: return batch_blocks_bf16(gi_mode);
+    case LBM_STORAGE_F64: return batch_blocks_f64(gi_mode);
+    default: return batch_blocks_f32(gi_mode);
+    }
+}
+}  // namespace lbm
+
+using namespace lbm;
+
+namespace {
+
+struct Slot {
+    bool used = false;
+    long id = 0;
+    int nx = 0, ny = 0, pitch = 0;
+    long long plane = 0;
+    void *f[2] = {nullptr, nullptr};
+    double *snap = nullptr;  // 2 * nx * ny: ux then uy
+    uint8_t *solid = nullptr;
+    size_t bytes = 0;
+    StepParams p{};
+    bool running = false;
+    double tol = 0;
+    long max_steps = 0;
+    int res_blocks = 1;
+};
+
+struct Pending {
+    long id;
+    lbm_request req;
+    std::vector<uint8_t> solid;
+};
+
+struct Record {
+    int slot = -1;
+    int state = LBM_REQ_QUEUED;
+    long steps = 0;
+    double residual = INFINITY;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct lbm_batch {
+    int storage = LBM_STORAGE_F16;
+    int gi_mode = LBM_GI_FULL;
+    size_t budget = 0, used = 0;
+    int max_slots = 1024;
+    int check_every = 1000;
+    int Ly_option = 0;
+    int Ly = 24;
+    bool tuned = false;
+    int parity = 0;
+    int num_sms = 1;
+    std::vector<Slot> slots;
+    std::vector<DomainDesc> h_desc;
+    DomainDesc *d_desc = nullptr;
+    int *d_active = nullptr, *d_prefix = nullptr;
+    unsigned int *d_step0 = nullptr, *h_step0 = nullptr;  // per active index: steps done (h_ pinned)
+    int sround = 1;
+    BatchState *d_state = nullptr;
+    int *h_active = nullptr, *h_prefix = nullptr;  // pinned
+    BatchState *h_state = nullptr;                 // pinned
+    unsigned int *d_work = nullptr;
+    int *d_err = nullptr;
+    double *d_sums = nullptr, *d_partials = nullptr, *h_sums = nullptr;
+    cudaStream_t stream = nullptr, io_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_K = 0;
+    std::chrono::steady_clock::time_point t0;
+    std::mutex mu;      // queue, records, slot bookkeeping
+    std::mutex run_mu;  // one tick at a time
+    std::deque<Pending> queue;
+    std::unordered_map<long, Record> records;
+    long next_id = 1;
+    std::thread engine;
+    std::atomic<bool> stop{false};
+    std::condition_variable cv;
+    bool engine_on = false;
+    double cell_updates = 0;
+    long launches = 0, ticks = 0;
+    std::string engine_error;
+};
+
+namespace {
+
+double seconds(const lbm_batch *b)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - b->t0).count();
+}
+
+lbm_status bfail(lbm_status s, const std::string &m) { return set_error(s, m); }
+
+size_t footprint(const lbm_batch *b, int nx, int ny, bool solid)
+{
+    const size_t pitch = (size_t)(nx + 63) / 64 * 64;
+    const size_t plane = pitch * ny;
+    return 2 * 9 * plane * storage_bytes(b->storage) + 2 * (size_t)nx * ny * sizeof(double) + (solid ? plane : 0);
+}
+
+void free_slot(Slot &s)
+{
+    if (s.f[0]) cudaFree(s.f[0]);
+    if (s.f[1]) cudaFree(s.f[1]);
+    if (s.snap) cudaFree(s.snap);
+    if (s.solid) cudaFree(s.solid);
+    s = Slot();
+}
+
+void set_geometry(StepParams &p, int Ly)
+{
+    p.nstrips = (p.nx + WS - 1) / WS;
+    p.Ly = Ly < p.ny ? Ly : p.ny;
+    p.nitems = p.nstrips * ((p.ny + p.Ly - 1) / p.Ly);
+}
+
+// Allocate and initialise one admitted request (rest state, lid or walls).
+lbm_status admit(lbm_batch *b, int si, const Pending &q)
+{
+    Slot &s = b->slots[si];
+    const lbm_request &r = q.req;
+    s.used = true;
+    s.id = q.id;
+    s.nx = r.nx;
+    s.ny = r.ny;
+    s.pitch = (r.nx + 63) / 64 * 64;
+    s.plane = (long long)s.pitch * r.ny;
+    s.bytes = footprint(b, r.nx, r.ny, !q.solid.empty());
+    const size_t pb = 9 * (size_t)s.plane * storage_bytes(b->storage);
+    const size_t N = (size_t)r.nx * r.ny;
+    if (cudaMalloc(&s.f[0], pb) != cudaSuccess || cudaMalloc(&s.f[1], pb) != cudaSuccess ||
+        cudaMalloc((void **)&s.snap, 2 * N * sizeof(double)) != cudaSuccess ||
+        (!q.solid.empty() && cudaMalloc((void **)&s.solid, (size_t)s.plane) != cudaSuccess)) {
+        cudaGetLastError();
+        free_slot(s);
+        return LBM_ERR_OOM;
+    }
+    if (s.solid) {
+        std::vector<uint8_t> h((size_t)s.plane, 0);
+        for (int y = 0; y < r.ny; ++y)
+            for (int x = 0; x < r.nx; ++x) h[(size_t)y * s.pitch + x] = q.solid[(size_t)y * r.nx + x] ? 1 : 0;
+        if (cudaMemcpy(s.solid, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            free_slot(s);
+            return LBM_ERR_CUDA;
+        }
+    }
+    // parameters (the same derivation as lbm_create / make_params)
+    lbm_side sides[4];
+    if (r.use_bnd) {
+        sides[0] = r.bnd.west;
+        sides[1] = r.bnd.east;
+        sides[2] = r.bnd.south;
+        sides[3] = r.bnd.north;
+    } else {
+        sides[0] = sides[1] = sides[2] = lbm_side{LBM_SIDE_WALL, 0.0, 0.0};
+        sides[3] = lbm_side{LBM_SIDE_MOVING_WALL, r.U, 0.0};
+    }
+    StepParams &p = s.p;
+    memset(&p, 0, sizeof(p));
+    p.nx = r.nx;
+    p.ny = r.ny;
+    p.pitch = s.pitch;
+    p.plane = s.plane;
+    p.perx = sides[0].kind == LBM_SIDE_PERIODIC;
+    p.pery = sides[2].kind == LBM_SIDE_PERIODIC;
+    p.gi_mode = b->gi_mode;
+    p.gamma = r.gamma;
+    double w[9] = {0, 0, 0, 1, 1, 1, 1, 1, 1};
+    w[4] = w[5] = 1.0 / (3.0 * r.nu / r.gamma + 0.5);
+    p.w3 = w[3];
+    p.w4 = w[4];
+    p.w5 = w[5];
+    p.w6 = w[6];
+    p.w7 = w[7];
+    p.w8 = w[8];
+    for (int k = 0; k < 4; ++k) {
+        const bool moving = sides[k].kind == LBM_SIDE_MOVING_WALL;
+        p.side_u[k][0] = moving ? sides[k].ux : 0.0;
+        p.side_u[k][1] = moving ? sides[k].uy : 0.0;
+    }
+    p.Fx = r.fx;
+    p.Fy = r.fy;
+    p.solid = s.solid;
+    p.sround = b->sround;
+    p.cf.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
+    p.cd.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
+    set_geometry(p, b->Ly);
+    s.tol = r.tol;
+    s.max_steps = r.max_steps;
+    s.res_blocks = residual_blocks(p);
+    // descriptor table entry
+    DomainDesc &d = b->h_desc[si];
+    memset(&d, 0, sizeof(d));
+    for (int k = 0; k < 2; ++k)
+        if (make_tensor_maps(&d.tload[k], &d.tstore[k], b->storage, s.f[k], r.nx, r.ny, s.pitch, s.plane) !=
+            cudaSuccess) {
+            free_slot(s);
+            return LBM_ERR_CUDA;
+        }
+    d.p = p;
+    d.f[0] = s.f[0];
+    d.f[1] = s.f[1];
+    d.forced = r.fx != 0.0 || r.fy != 0.0;
+    cudaError_t e = cudaMemcpyAsync(b->d_desc + si, &d, sizeof(DomainDesc), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = launch_init_eq(p, b->storage, nullptr, nullptr, nullptr, s.f[b->parity], b->stream);
+    if (e == cudaSuccess)
+        e = launch_residual(p, b->storage, s.f[b->parity], s.snap, s.snap + N, b->d_partials, s.res_blocks,
+                            b->d_sums + 5 * si, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // h_desc entry may change later
+    if (e != cudaSuccess) {
+        free_slot(s);
+        return LBM_ERR_CUDA;
+    }
+    s.running = true;
+    return LBM_OK;
+}
+
+void admit_pending(lbm_batch *b)
+{
+    for (;;) {
+        Pending q;
+        int si = -1;
+        {
+            std::lock_guard<std::mutex> lk(b->mu);
+            if (b->queue.empty()) return;
+            const Pending &head = b->queue.front();
+            const size_t need = footprint(b, head.req.nx, head.req.ny, !head.solid.empty());
+            if (b->used + need > b->budget) return;  // FIFO: the head waits for memory
+            for (int k = 0; k < b->max_slots; ++k)
+                if (!b->slots[k].used) {
+                    si = k;
+                    break;
+                }
+            if (si < 0) return;
+            q = std::move(b->queue.front());
+            b->queue.pop_front();
+            b->slots[si].used = true;  // reserve
+            b->used += need;
+        }
+        const lbm_status st = admit(b, si, q);
+        std::lock_guard<std::mutex> lk(b->mu);
+        Record &rec = b->records[q.id];
+        if (st != LBM_OK) {
+            b->used -= footprint(b, q.req.nx, q.req.ny, !q.solid.empty());
+            b->slots[si] = Slot();
+            rec.state = LBM_REQ_FAILED;
+            rec.t_admit = rec.t_done = seconds(b);
+        } else {
+            rec.slot = si;
+            rec.state = LBM_REQ_RUNNING;
+            rec.t_admit = seconds(b);
+        }
+    }
+}
+
+// Upload the active list and the item prefix sums; returns the active count.
+int build_active(lbm_batch *b, double &cells)
+{
+    int n = 0, total = 0;
+    cells = 0;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        for (int k = 0; k < b->max_slots; ++k) {
+            const Slot &s = b->slots[k];
+            if (!s.used || !s.running) continue;
+            b->h_active[n] = k;
+            b->h_prefix[n] = total;
+            b->h_step0[n] = (unsigned int)b->records[s.id].steps;
+            total += s.p.nitems;
+            cells += (double)s.nx * s.ny;
+            ++n;
+        }
+    }
+    b->h_prefix[n] = total;
+    b->h_state->n_active = n;
+    b->h_state->total_items = total;
+    cudaMemcpyAsync(b->d_active, b->h_active, (size_t)(n > 0 ? n : 1) * sizeof(int), cudaMemcpyHostToDevice,
+                    b->stream);
+    cudaMemcpyAsync(b->d_prefix, b->h_prefix, (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(b->d_step0, b->h_step0, (size_t)(n > 0 ? n : 1) * sizeof(unsigned int), cudaMemcpyHostToDevice,
+                    b->stream);
+    cudaMemcpyAsync(b->d_state, b->h_state, sizeof(BatchState), cudaMemcpyHostToDevice, b->stream);
+    return n;
+}
+
+BatchArgs batch_args(const lbm_batch *b, int parity, int k)
+{
+    BatchArgs a;
+    a.domains = b->d_desc;
+    a.active = b->d_active;
+    a.prefix = b->d_prefix;
+    a.state = b->d_state;
+    a.work = b->d_work;
+    a.error = b->d_err;
+    a.parity = parity;
+    a.step0 = b->d_step0;
+    a.k = k;
+    return a;
+}
+
+int batch_grid(const lbm_batch *b) { return b->num_sms * batch_blocks_per_sm(b->storage, b->gi_mode); }
+
+// Set the rows per item of every running domain and re-upload their descriptors.
+void apply_Ly(lbm_batch *b, int Ly)
+{
+    b->Ly = Ly;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        for (int k = 0; k < b->max_slots; ++k) {
+            Slot &s = b->slots[k];
+            if (!s.used || !s.running) continue;
+            set_geometry(s.p, Ly);
+            b->h_desc[k].p = s.p;
+            cudaMemcpyAsync(&b->d_desc[k].p, &b->h_desc[k].p, sizeof(StepParams), cudaMemcpyHostToDevice,
+                            b->stream);
+        }
+    }
+    cudaStreamSynchronize(b->stream);
+}
+
+// Pick the rows per item (the tile height of a warp's work item) by timing a
+// few steps of the current batch for each candidate.  The steps taken count.
+lbm_status autotune(lbm_batch *b)
+{
+    const int cand[5] = {8, 12, 16, 24, 32};
+    float best_ms = 1e30f;
+    int best = b->Ly;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LBM_ERR_CUDA;
+    const int reps = 4;  // even: the parity is unchanged
+    const int grid = batch_grid(b);
+    for (int c : cand) {
+        apply_Ly(b, c);
+        double cells;
+        build_active(b, cells);
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps; ++r)
+            launch_batch_step(b->storage, b->gi_mode, batch_args(b, (b->parity + r) & 1, r), grid, b->stream);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return LBM_ERR_CUDA;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        b->launches += reps;
+        b->cell_updates += cells * reps;
+        std::lock_guard<std::mutex> lk(b->mu);
+        for (int k = 0; k < b->max_slots; ++k)
+            if (b->slots[k].used && b->slots[k].running) b->records[b->slots[k].id].steps += reps;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    apply_Ly(b, best);
+    b->tuned = true;
+    return LBM_OK;
+}
+
+lbm_status ensure_graph(lbm_batch *b)
+{
+    if (b->graph && b->graph_K == b->check_every) return LBM_OK;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    const int grid = batch_grid(b);  // occupancy query before the capture starts
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
+    for (int k = 0; k < b->check_every; ++k)
+        launch_batch_step(b->storage, b->gi_mode, batch_args(b, (b->parity + k) & 1, k), grid, b->stream);
+    if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess) return LBM_ERR_CUDA;
+    const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return LBM_ERR_CUDA;
+    }
+    b->graph_K = b->check_every;
+    return LBM_OK;
+}
+
+// One engine tick; *busy tells whether anything was running or admitted.
+lbm_status tick(lbm_batch *b, bool *busy)
+{
+    std::lock_guard<std::mutex> run_lock(b->run_mu);
+    admit_pending(b);
+    double cells = 0;
+    int n = build_active(b, cells);
+    *busy = n > 0;
+    if (n == 0) return LBM_OK;
+    if (!b->tuned && b->Ly_option <= 0) {
+        lbm_status st = autotune(b);
+        if (st != LBM_OK) return bfail(st, "batch autotune failed");
+        n = build_active(b, cells);
+    }
+    if (ensure_graph(b) != LBM_OK) return bfail(LBM_ERR_CUDA, "batch graph capture failed");
+    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    // convergence residual of every running domain (FP64)
+    for (int i = 0; i < n; ++i) {
+        const int k = b->h_active[i];
+        Slot &s = b->slots[k];
+        const size_t N = (size_t)s.nx * s.ny;
+        e = launch_residual(s.p, b->storage, s.f[b->parity], s.snap, s.snap + N, b->d_partials, s.res_blocks,
+                            b->d_sums + 5 * k, b->stream);
+        if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, "batch residual launch failed");
+    }
+    cudaMemcpyAsync(b->h_sums, b->d_sums, (size_t)b->max_slots * 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                    b->stream);
+    int err = 0;
+    e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, std::string("batch tick: ") + cudaGetErrorString(e));
+    cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        cudaMemset(b->d_work, 0, 2 * sizeof(unsigned int));
+        return bfail(LBM_ERR_CUDA, "a batched step kernel's bounded wait expired");
+    }
+    b->launches += b->check_every;
+    b->cell_updates += cells * b->check_every;
+    b->ticks += 1;
+    const double t = seconds(b);
+    std::lock_guard<std::mutex> lk(b->mu);
+    for (int i = 0; i < n; ++i) {
+        const int k = b->h_active[i];
+        Slot &s = b->slots[k];
+        Record &rec = b->records[s.id];
+        rec.steps += b->check_every;
+        const double du2 = b->h_sums[5 * k], u2 = b->h_sums[5 * k + 1];
+        double r;
+        if (!isfinite(du2) || !isfinite(u2)) r = NAN;
+        else if (u2 == 0.0) r = du2 == 0.0 ? 0.0 : INFINITY;
+        else r = sqrt(du2 / u2);
+        rec.residual = r;
+        int state = LBM_REQ_RUNNING;
+        if (!isfinite(r) && !(r == INFINITY)) state = LBM_REQ_DIVERGED;
+        else if (r < s.tol) state = LBM_REQ_CONVERGED;
+        else if (rec.steps >= s.max_steps) state = LBM_REQ_NOT_CONVERGED;
+        if (state != LBM_REQ_RUNNING) {
+            s.running = false;
+            rec.state = state;
+            rec.t_done = t;
+        }
+    }
+    return LBM_OK;
+}
+
+void engine_loop(lbm_batch *b)
+{
+    while (!b->stop.load()) {
+        bool busy = false;
+        const lbm_status st = tick(b, &busy);
+        if (st != LBM_OK) {
+            std::lock_guard<std::mutex> lk(b->mu);
+            b->engine_error = lbm_last_error();
+            for (auto &kv : b->records)
+                if (kv.second.state == LBM_REQ_RUNNING || kv.second.state == LBM_REQ_QUEUED) {
+                    kv.second.state = LBM_REQ_FAILED;
+                    kv.second.t_done = seconds(b);
+                }
+            return;
+        }
+        if (!busy) {
+            std::unique_lock<std::mutex> lk(b->mu);
+            b->cv.wait_for(lk, std::chrono::milliseconds(1));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(size_t hbm_budget_bytes, int storage, int gi_mode, lbm_batch **out)
+{
+    if (!out) return bfail(LBM_ERR_INVALID, "out is null");
+    *out = nullptr;
+    if (storage < 0 || storage > 3) return bfail(LBM_ERR_INVALID, "storage must be 0..3");
+    if (gi_mode < 0 || gi_mode > 2) return bfail(LBM_ERR_INVALID, "gi_mode must be 0..2");
+    if (hbm_budget_bytes == 0) return bfail(LBM_ERR_INVALID, "budget must be > 0");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(LBM_ERR_CUDA, "no usable CUDA device");
+    }
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return bfail(LBM_ERR_OOM, "host allocation failed");
+    b->storage = storage;
+    b->gi_mode = gi_mode;
+    b->budget = hbm_budget_bytes;
+    b->t0 = std::chrono::steady_clock::now();
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    b->slots.resize(b->max_slots);
+    b->h_desc.resize(b->max_slots);
+    bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->io_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_desc, (size_t)b->max_slots * sizeof(DomainDesc)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_active, (size_t)b->max_slots * sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_prefix, (size_t)(b->max_slots + 1) * sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_step0, (size_t)b->max_slots * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_step0, (size_t)b->max_slots * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_state, sizeof(BatchState)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_work, 2 * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_err, sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_sums, (size_t)b->max_slots * 5 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_partials, 1024 * 5 * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_sums, (size_t)b->max_slots * 5 * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_active, (size_t)b->max_slots * sizeof(int)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_prefix, (size_t)(b->max_slots + 1) * sizeof(int)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_state, sizeof(BatchState)) == cudaSuccess;
+    if (ok) {
+        ok = cudaMemset(b->d_work, 0, 2 * sizeof(unsigned int)) == cudaSuccess &&
+             cudaMemset(b->d_err, 0, sizeof(int)) == cudaSuccess &&
+             cudaMemset(b->d_sums, 0, (size_t)b->max_slots * 5 * sizeof(double)) == cudaSuccess;
+        b->h_state->n_active = 0;
+        b->h_state->total_items = 0;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        lbm_batch_destroy(b);
+        return bfail(LBM_ERR_OOM, "batch allocation failed");
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_option(lbm_batch *b, const char *key, double v)
+{
+    if (!b || !key) return bfail(LBM_ERR_INVALID, "null argument");
+    const std::string k(key);
+    std::lock_guard<std::mutex> run_lock(b->run_mu);
+    if (k == "check_every") {
+        const int K = (int)v;
+        if (K < 2 || K % 2 || K > 100000) return bfail(LBM_ERR_INVALID, "check_every must be even, 2..100000");
+        b->check_every = K;
+    } else if (k == "stochastic_rounding") {
+        b->sround = v != 0.0;  // domains admitted from now on
+    } else if (k == "rows_per_item") {
+        if (v < 0 || v > 65535) return bfail(LBM_ERR_INVALID, "rows_per_item must be 0..65535");
+        b->Ly_option = (int)v;
+        if (b->Ly_option > 0) {
+            apply_Ly(b, b->Ly_option);
+            b->tuned = true;
+        } else {
+            b->tuned = false;
+        }
+    } else {
+        return bfail(LBM_ERR_INVALID, "unknown batch option: " + k);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_submit(lbm_batch *b, const lbm_request *req, long *id)
+{
+    if (!b || !req) return bfail(LBM_ERR_INVALID, "null argument");
+    if (req->nx < 3 || req->ny < 3 || req->ny > 65535) return bfail(LBM_ERR_INVALID, "bad domain size");
+    if (!(req->nu > 0) || !(req->gamma > 0 && req->gamma <= 1)) return bfail(LBM_ERR_INVALID, "bad nu or gamma");
+    const double w = 1.0 / (3.0 * req->nu / req->gamma + 0.5);
+    if (!(w > 0 && w < 2)) return bfail(LBM_ERR_INVALID, "omega4 out of (0, 2)");
+    if (!(req->tol > 0) || req->max_steps <= 0) return bfail(LBM_ERR_INVALID, "tol and max_steps must be > 0");
+    if (req->use_bnd) {
+        const lbm_side *sd[4] = {&req->bnd.west, &req->bnd.east, &req->bnd.south, &req->bnd.north};
+        for (int k = 0; k < 4; ++k)
+            if (sd[k]->kind < 0 || sd[k]->kind > 2) return bfail(LBM_ERR_INVALID, "bad side kind");
+        if ((sd[0]->kind == LBM_SIDE_PERIODIC) != (sd[1]->kind == LBM_SIDE_PERIODIC) ||
+            (sd[2]->kind == LBM_SIDE_PERIODIC) != (sd[3]->kind == LBM_SIDE_PERIODIC))
+            return bfail(LBM_ERR_INVALID, "opposite sides must both be periodic or both walls");
+    }
+    Pending q;
+    q.req = *req;
+    if (req->use_bnd && req->bnd.solid)
+        q.solid.assign(req->bnd.solid, req->bnd.solid + (size_t)req->nx * req->ny);
+    q.req.bnd.solid = nullptr;
+    if (footprint(b, req->nx, req->ny, !q.solid.empty()) > b->budget)
+        return bfail(LBM_ERR_INVALID, "request larger than the batch budget");
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        q.id = b->next_id++;
+        Record &rec = b->records[q.id];
+        rec.t_submit = seconds(b);
+        if (id) *id = q.id;
+        b->queue.push_back(std::move(q));
+    }
+    b->cv.notify_all();
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_poll(lbm_batch *b, long id, int *done, lbm_result *res)
+{
+    if (!b) return bfail(LBM_ERR_INVALID, "null batch");
+    std::lock_guard<std::mutex> lk(b->mu);
+    auto it = b->records.find(id);
+    if (it == b->records.end()) return bfail(LBM_ERR_INVALID, "unknown request id");
+    const Record &r = it->second;
+    if (done) *done = r.state >= LBM_REQ_CONVERGED;
+    if (res) {
+        res->state = r.state;
+        res->steps = r.steps;
+        res->residual = r.residual;
+        res->t_submit = r.t_submit;
+        res->t_admit = r.t_admit;
+        res->t_done = r.t_done;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_fields(lbm_batch *b, long id, double *rho, double *ux, double *uy)
+{
+    if (!b) return bfail(LBM_ERR_INVALID, "null batch");
+    Slot s;
+    int parity;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        auto it = b->records.find(id);
+        if (it == b->records.end()) return bfail(LBM_ERR_INVALID, "unknown request id");
+        if (it->second.state < LBM_REQ_CONVERGED || it->second.slot < 0)
+            return bfail(LBM_ERR_INVALID, "request not finished (or released)");
+        s = b->slots[it->second.slot];
+        parity = b->parity;
+    }
+    const size_t N = (size_t)s.nx * s.ny;
+    double *d = nullptr;
+    if (cudaMalloc((void **)&d, 3 * N * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(LBM_ERR_OOM, "device allocation failed (fields)");
+    }
+    cudaError_t e = launch_fields(s.p, b->storage, s.f[parity], d, d + N, d + 2 * N, b->io_stream);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, d, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
+    if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, d + N, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
+    if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->io_stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, std::string("batch fields: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_release(lbm_batch *b, long id)
+{
+    if (!b) return bfail(LBM_ERR_INVALID, "null batch");
+    Slot s;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        auto it = b->records.find(id);
+        if (it == b->records.end()) return bfail(LBM_ERR_INVALID, "unknown request id");
+        if (it->second.state < LBM_REQ_CONVERGED) return bfail(LBM_ERR_INVALID, "request not finished");
+        const int si = it->second.slot;
+        if (si >= 0) {
+            s = b->slots[si];
+            b->slots[si] = Slot();
+            b->used -= s.bytes;
+        }
+        b->records.erase(it);
+    }
+    free_slot(s);
+    b->cv.notify_all();
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_run(lbm_batch *b, double wall_seconds)
+{
+    if (!b) return bfail(LBM_ERR_INVALID, "null batch");
+    if (b->engine_on) return bfail(LBM_ERR_INVALID, "the background engine is running");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        bool busy = false;
+        const lbm_status st = tick(b, &busy);
+        if (st != LBM_OK) return st;
+        if (!busy) {
+            std::lock_guard<std::mutex> lk(b->mu);
+            if (b->queue.empty()) return LBM_OK;
+            // the queue head does not fit and nothing runs: it never will
+            return bfail(LBM_ERR_OOM, "queued request cannot be admitted (release finished requests)");
+        }
+        if (wall_seconds > 0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > wall_seconds)
+            return bfail(LBM_ERR_TIMEOUT, "wall-clock limit reached");
+    }
+}
+
+lbm_status lbm_batch_start(lbm_batch *b)
+{
+    if (!b) return bfail(LBM_ERR_INVALID, "null batch");
+    if (b->engine_on) return LBM_OK;
+    b->stop = false;
+    b->engine = std::thread(engine_loop, b);
+    b->engine_on = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_stop(lbm_batch *b)
+{
+    if (!b) return bfail(LBM_ERR_INVALID, "null batch");
+    if (!b->engine_on) return LBM_OK;
+    b->stop = true;
+    b->cv.notify_all();
+    b->engine.join();
+    b->engine_on = false;
+    if (!b->engine_error.empty()) return bfail(LBM_ERR_CUDA, b->engine_error);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_stats(lbm_batch *b, double stats[6])
+{
+    if (!b || !stats) return bfail(LBM_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(b->mu);
+    int running = 0;
+    for (const auto &kv : b->records) running += kv.second.state == LBM_REQ_RUNNING;
+    stats[0] = b->cell_updates;
+    stats[1] = (double)b->launches;
+    stats[2] = (double)b->ticks;
+    stats[3] = running;
+    stats[4] = (double)b->queue.size();
+    stats[5] = (double)b->used;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return;
+    lbm_batch_stop(b);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &s : b->slots)
+        if (s.used) free_slot(s);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_active);
+    cudaFree(b->d_prefix);
+    cudaFree(b->d_step0);
+    if (b->h_step0) cudaFreeHost(b->h_step0);
+    cudaFree(b->d_state);
+    cudaFree(b->d_work);
+    cudaFree(b->d_err);
+    cudaFree(b->d_sums);
+    cudaFree(b->d_partials);
+    if (b->h_sums) cudaFreeHost(b->h_sums);
+    if (b->h_active) cudaFreeHost(b->h_active);
+    if (b->h_prefix) cudaFreeHost(b->h_prefix);
+    if (b->h_state) cudaFreeHost(b->h_state);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->io_stream) cudaStreamDestroy(b->io_stream);
+    delete b;
+}
+
+}  // extern "C"

@@ -29,30 +29,77 @@ __host__ __device__ constexpr double weight(int a) { return a == 0 ? 4.0 / 9.0 :
 
 // ---- storage conversion ------------------------------------------------------
 template <typename ST> struct StorageTraits;
+//
+// 16-bit types also have store_sr: stochastic rounding of an FP32 value with
+// 32 random bits r.  The top (23 - kept mantissa bits) bits of r are added to
+// the magnitude's dropped bits and the sum is truncated, so the value rounds
+// up with probability equal to its distance from the lower neighbour: the
+// rounding error has zero mean whatever the state.  (Round-to-nearest errors
+// are a fixed function of the state; in a near-steady flow they act as a
+// constant forcing that the slowest viscous modes amplify by about
+// 1/(nu k^2).)  Values so small that the 16-bit result is subnormal would
+// drop more bits than r covers; FP16 storage is scaled so that only
+// |g| < 2^-28 gets there.
 template <> struct StorageTraits<float> {
     using R = float;
+    static constexpr bool kReduced = false;
     __device__ static __forceinline__ float load(const float *p) { return __ldg(p); }
     __device__ static __forceinline__ float cvt(float v) { return v; }
     __device__ static __forceinline__ void store(float *p, float v) { *p = v; }
+    __device__ static __forceinline__ void store_sr(float *p, float v, uint32_t) { *p = v; }
 };
 template <> struct StorageTraits<double> {
     using R = double;
+    static constexpr bool kReduced = false;
     __device__ static __forceinline__ double load(const double *p) { return __ldg(p); }
     __device__ static __forceinline__ double cvt(double v) { return v; }
     __device__ static __forceinline__ void store(double *p, double v) { *p = v; }
+    __device__ static __forceinline__ void store_sr(double *p, double v, uint32_t) { *p = v; }
 };
-template <> struct StorageTraits<__half> {
+template <> struct StorageTraits<__half> {  // holds F16_SCALE * g
     using R = float;
-    __device__ static __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
-    __device__ static __forceinline__ float cvt(__half v) { return __half2float(v); }
-    __device__ static __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
+    static constexpr bool kReduced = true;
+    __device__ static __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)) * F16_INV_SCALE; }
+    __device__ static __forceinline__ float cvt(__half v) { return __half2float(v) * F16_INV_SCALE; }
+    __device__ static __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v * F16_SCALE); }
+    __device__ static __forceinline__ void store_sr(__half *p, float v, uint32_t r)
+    {
+        // 13 dropped bits for a normal FP16 result
+        *p = __float2half_rz(__uint_as_float(__float_as_uint(v * F16_SCALE) + (r >> 19)));
+    }
 };
 template <> struct StorageTraits<__nv_bfloat16> {
     using R = float;
+    static constexpr bool kReduced = true;
     __device__ static __forceinline__ float load(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     __device__ static __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ void store_sr(__nv_bfloat16 *p, float v, uint32_t r)
+    {
+        *p = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r >> 16)));  // 16 dropped bits
+    }
 };
+
+// 32-bit integer hash for the rounding bits: Wellons' "lowbias32"
+// xorshift-multiply finaliser (hash-prospector), a bijection on 32 bits.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Per-direction odd multipliers: direction a of a cell takes the top bits of
+// h * kSrMul[a], where h = mix32(mix32(step) ^ cell).
+__device__ __forceinline__ uint32_t sr_bits(uint32_t h, int a)
+{
+    constexpr uint32_t m[9] = {0x9e3779b1u, 0x85ebca77u, 0xc2b2ae3du, 0x27d4eb2fu, 0x165667b1u,
+                               0xd3a2646du, 0xfd7046c5u, 0xb55a4f09u, 0x1b873593u};
+    return h * m[a];
+}
 
 // Reciprocal: correctly rounded in FP32 (no IEEE division sequence), exact
 // division in FP64.

@@ -17,6 +17,14 @@ constexpr int WS = 32;
 constexpr int WARPS = 4;
 constexpr int THREADS = 32 * WARPS;  // threads per block of the step kernel
 
+// FP16 storage holds 2^14 g rather than g (an exact power-of-two scale): the
+// deviations of slow regions (|g| down to about 1e-8) then stay in the normal
+// FP16 range, where rounding has the full 11-bit precision and stochastic
+// rounding is exact; |2^14 g| stays far below the FP16 maximum 65504 for any
+// stable flow (|g| < 4).
+constexpr float F16_SCALE = 16384.0f;
+constexpr float F16_INV_SCALE = 1.0f / 16384.0f;
+
 // Collision constants in the compute precision, filled on the host once per
 // launch (no FP64 arithmetic in the FP32 kernels).
 template <typename R>
@@ -80,8 +88,40 @@ struct StepParams {
     unsigned int *work;      // device work counters {next item, warps done}, zero between launches
     // work decomposition: items = warp strips x segments, each segment Ly rows
     int Ly, nstrips, nitems;
+    // 16-bit storage: round the stored deviations stochastically (nonzero) or
+    // to nearest; the random bits are a hash of (step, cell, direction)
+    int sround;
+    unsigned int step;       // step index of this launch (low 32 bits), single-domain kernel
     Consts<float> cf;
     Consts<double> cd;
+};
+
+// One domain of a batch, in device memory (TMA descriptors need 64-byte alignment).
+struct alignas(128) DomainDesc {
+    CUtensorMap tload[2];   // load descriptors of f[0], f[1]
+    CUtensorMap tstore[2];  // store descriptors of f[0], f[1]
+    StepParams p;           // the domain's parameters (work/error pointers unused)
+    const void *f[2];       // population buffers
+    int forced;             // nonzero: a body force acts (uniform Fx, Fy)
+};
+
+// Active set of a batch, read by the kernel each launch (so a captured graph
+// stays valid while domains join and retire).
+struct BatchState {
+    int n_active;     // active domains
+    int total_items;  // prefix[n_active]
+};
+
+struct BatchArgs {
+    const DomainDesc *domains;  // all slots
+    const int *active;          // active slot ids, n_active of them
+    const int *prefix;          // item prefix sums over the active slots (n_active + 1)
+    const BatchState *state;
+    unsigned int *work;         // work counters {next item, warps done}
+    int *error;
+    int parity;                 // source buffer of this step (all domains step together)
+    const unsigned int *step0;  // per active index: the domain's step count at the start of the tick
+    int k;                      // launch index within the tick (domain step = step0 + k)
 };
 
 // The launchers below are defined per storage type (one translation unit each).
@@ -91,6 +131,8 @@ cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const C
 cudaError_t launch_step_f16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
 cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
 cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
+cudaError_t launch_batch_step(int storage, int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
+int batch_blocks_per_sm(int storage, int gi_mode);
 int blocks_per_sm_f32(int gi_mode);
 int blocks_per_sm_f16(int gi_mode);
 int blocks_per_sm_bf16(int gi_mode);

@@ -9,6 +9,13 @@ cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const C
     return launch_step_t<float>(p, tin, tout, fin, grid, s);
 }
 
+cudaError_t launch_batch_f32(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s)
+{
+    return launch_batch_t<float>(gi_mode, a, grid, s);
+}
+
+int batch_blocks_f32(int gi_mode) { return batch_blocks_t<float>(gi_mode); }
+
 int blocks_per_sm_f32(int gi_mode) { return blocks_per_sm_t<float>(gi_mode); }
 
 }  // namespace lbm

@@ -140,51 +140,64 @@ constexpr uint64_t OPP_PACK = 0ull | (3ull << 4) | (4ull << 8) | (1ull << 12) | 
 
 template <bool V> struct Flag { static constexpr bool value = V; };
 
-template <typename ST, int MODE, bool FORCED>
-__global__ void __launch_bounds__(THREADS, MinBlocks<ST>::value)
-stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap tin,
-                      const __grid_constant__ CUtensorMap tout, const ST *__restrict__ fin)
+// Per-warp state that lives across work items.
+struct WarpCtx {
+    int lane;
+    unsigned char *ws;            // this warp's ring, stage and barriers
+    uint32_t ring_u32, stage_u32, bars_u32;
+    uint32_t q_base;              // sequence number of the current item's first source row
+    int issued;                   // item rows issued so far (lane 0)
+    int h_side, h_a, h_ex, h_ey;  // lane-parallel halo: side and direction of this lane
+};
+
+template <typename ST>
+__device__ __forceinline__ void warp_begin(WarpCtx &w, unsigned char *smem)
 {
     using T = Tile<ST>;
-    using R = typename StorageTraits<ST>::R;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    unsigned char *ws = smem + warp * T::WARP_BYTES;  // this warp's ring, stage and barriers
-    const uint32_t ring_u32 = smem_u32(ws);
-    const uint32_t stage_u32 = ring_u32 + T::STAGE_OFF;
-    const uint32_t bars_u32 = ring_u32 + T::BAR_OFF;
-    ST *stage = reinterpret_cast<ST *>(ws + T::STAGE_OFF);
-    const unsigned FULL = 0xffffffffu;
-
-    if (lane == 0) {
-        for (int k = 0; k < T::NSLOT; ++k) mbar_init(bars_u32 + 8 * k, 1);
+    w.lane = threadIdx.x & 31;
+    w.ws = smem + (threadIdx.x >> 5) * T::WARP_BYTES;
+    w.ring_u32 = smem_u32(w.ws);
+    w.stage_u32 = w.ring_u32 + T::STAGE_OFF;
+    w.bars_u32 = w.ring_u32 + T::BAR_OFF;
+    w.q_base = 0;
+    w.issued = 0;
+    // lane-parallel halo density: lane l < 9 handles direction l of the left
+    // halo cell (x0 - 1), lane 16 + l of the right one (x0 + WS)
+    w.h_side = w.lane >> 4;
+    w.h_a = w.lane & 15;
+    w.h_ex = w.h_a < 9 ? (int)((EX_PACK >> (2 * w.h_a)) & 3u) - 1 : 0;
+    w.h_ey = w.h_a < 9 ? (int)((EY_PACK >> (2 * w.h_a)) & 3u) - 1 : 0;
+    if (w.lane == 0) {
+        for (int k = 0; k < T::NSLOT; ++k) mbar_init(w.bars_u32 + 8 * k, 1);
         fence_mbar_init();
     }
     __syncwarp();
+}
 
+// One work item: rows [seg*Ly, ...) of the 32-column strip `strip` of the
+// domain described by p, reading fin through tin and writing through tout.
+// Returns false when a bounded wait expired (the caller then stops).
+template <typename ST, int MODE, bool FORCED>
+__device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const CUtensorMap *tin,
+                                         const CUtensorMap *tout, const ST *__restrict__ fin, int strip, int seg,
+                                         uint32_t step)
+{
+    using T = Tile<ST>;
+    using R = typename StorageTraits<ST>::R;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = w.lane;
+    unsigned char *ws = w.ws;
+    const uint32_t ring_u32 = w.ring_u32, stage_u32 = w.stage_u32, bars_u32 = w.bars_u32;
+    ST *stage = reinterpret_cast<ST *>(ws + T::STAGE_OFF);
+    const uint32_t q_base = w.q_base;
+    int &issued = w.issued;
+    const int h_side = w.h_side, h_a = w.h_a, h_ex = w.h_ex, h_ey = w.h_ey;
     const Consts<R> &c = consts<R>(p);
     const bool has_solid = p.solid != nullptr;
-    uint32_t q_base = 0;   // sequence number of the current item's first source row (this warp)
+    const bool sround = StorageTraits<ST>::kReduced && p.sround;
+    const uint32_t seed = sround ? mix32(step) : 0u;
     bool abort = false;
-    int issued = 0;        // item rows issued so far (lane 0)
-
-    // lane-parallel halo density: lane l < 9 handles direction l of the left
-    // halo cell (x0 - 1), lane 16 + l of the right one (x0 + WS)
-    const int h_side = lane >> 4, h_a = lane & 15;
-    const int h_ex = h_a < 9 ? (int)((EX_PACK >> (2 * h_a)) & 3u) - 1 : 0;
-    const int h_ey = h_a < 9 ? (int)((EY_PACK >> (2 * h_a)) & 3u) - 1 : 0;
-
-    // items are handed out dynamically (one atomic per item), so warps that
-    // finish early take more work and the slowest warp bounds the tail
-    auto next_item = [&]() -> int {
-        int it = 0;
-        if (lane == 0) it = (int)atomicAdd(p.work, 1u);
-        return __shfl_sync(FULL, it, 0);
-    };
-    for (int item = next_item(); item < p.nitems && !abort; item = next_item()) {
-        const int strip = item % p.nstrips;
-        const int seg = item / p.nstrips;
+    {
         const int x0 = strip * WS;
         const int y0 = seg * p.Ly;
         const int y1 = min(y0 + p.Ly, p.ny);
@@ -210,7 +223,7 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
                 mbar_arrive(bar);  // beyond a wall side: never read
             } else {
                 mbar_expect_tx(bar, (uint32_t)T::ROW_BYTES);
-                tma_load_3d(ring_u32 + slot * T::SLOT_BYTES, &tin, x0 - T::PAD, s, 0, bar);
+                tma_load_3d(ring_u32 + slot * T::SLOT_BYTES, tin, x0 - T::PAD, s, 0, bar);
             }
         };
         // all lanes: wait for item row k, patch periodic x halo columns
@@ -399,11 +412,8 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
             for (int k = 0; k < min(T::NSLOT, nsrc); ++k) issue(k);
             issued = min(T::NSLOT, nsrc);
         }
-        bool ok = land(0) && land(1) && land(2) && land(3);
-        if (!ok) {
-            abort = true;
-            break;
-        }
+        const bool ok = land(0) && land(1) && land(2) && land(3);
+        if (!ok) return false;
         // cur = populations of row y, nxt = row y + 1; densities of rows y-1, y, y+1
         R cur[9], nxt[9];
         bool cur_valid, nxt_valid;
@@ -467,13 +477,21 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
             // stage the row (the previous row's store must have read the buffer)
             if (lane == 0) bulk_wait_read_0();
             __syncwarp();
+            if (sround) {
+                const uint32_t h = mix32(seed ^ (uint32_t)(y * p.nx + x));
 #pragma unroll
-            for (int a = 0; a < 9; ++a)
-                StorageTraits<ST>::store(stage + a * WS + lane, (FAST || cur_valid) ? out[a] : R(0));
+                for (int a = 0; a < 9; ++a)
+                    StorageTraits<ST>::store_sr(stage + a * WS + lane, (FAST || cur_valid) ? out[a] : R(0),
+                                                sr_bits(h, a));
+            } else {
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+                    StorageTraits<ST>::store(stage + a * WS + lane, (FAST || cur_valid) ? out[a] : R(0));
+            }
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) {
-                tma_store_3d(&tout, x0, y, 0, stage_u32);
+                tma_store_3d(tout, x0, y, 0, stage_u32);
                 bulk_commit();
             }
 #pragma unroll
@@ -495,28 +513,160 @@ stream_collide_kernel(const StepParams p, const __grid_constant__ CUtensorMap ti
         for (int y = y0; y < yf0 && !abort; ++y) abort = !iter(Flag<false>(), y);
         for (int y = yf0; y < yf1 && !abort; ++y) abort = !iter(Flag<true>(), y);
         for (int y = max(yf1, yf0); y < y1 && !abort; ++y) abort = !iter(Flag<false>(), y);
-        if (abort) break;
-        q_base += (uint32_t)nsrc;
+        if (abort) return false;
+        w.q_base += (uint32_t)nsrc;
     }
-    if (abort && lane == 0) {
-        // record the failure and let this warp's copies in flight finish
-        atomicExch(p.error, 1);
-        for (int k = max(0, issued - T::NSLOT); k < issued; ++k) {
-            const uint32_t q = q_base + (uint32_t)k;
-            if (!mbar_wait_bounded(bars_u32 + 8 * (q % T::NSLOT), (q / T::NSLOT) & 1u)) break;
+    return true;
+}
+
+// End of a warp's work: on failure record it and let the warp's copies in
+// flight finish; wait for the stores; sign off on the work counter (the last
+// warp of the launch resets the counters for the next launch).
+template <typename ST>
+__device__ __forceinline__ void warp_end(WarpCtx &w, bool abort, int *error, unsigned int *work)
+{
+    using T = Tile<ST>;
+    if (abort && w.lane == 0) {
+        atomicExch(error, 1);
+        for (int k = max(0, w.issued - T::NSLOT); k < w.issued; ++k) {
+            const uint32_t q = w.q_base + (uint32_t)k;
+            if (!mbar_wait_bounded(w.bars_u32 + 8 * (q % T::NSLOT), (q / T::NSLOT) & 1u)) break;
         }
     }
-    if (lane == 0) {
+    if (w.lane == 0) {
         bulk_wait_all();  // stores done before the stage memory goes away
-        // sign off; the last warp of the launch resets the counters for the next one
         __threadfence();
         const unsigned total = gridDim.x * WARPS;
-        if (atomicAdd(p.work + 1, 1u) == total - 1) {
-            atomicExch(p.work, 0u);
-            atomicExch(p.work + 1, 0u);
+        if (atomicAdd(work + 1, 1u) == total - 1) {
+            atomicExch(work, 0u);
+            atomicExch(work + 1, 0u);
         }
     }
     __syncwarp();
+}
+
+// Items are handed out dynamically (one atomic per item), so warps that finish
+// early take more work and the slowest warp bounds the tail.
+__device__ __forceinline__ int next_item(const WarpCtx &w, unsigned int *work)
+{
+    int it = 0;
+    if (w.lane == 0) it = (int)atomicAdd(work, 1u);
+    return __shfl_sync(0xffffffffu, it, 0);
+}
+
+// One time step of one domain.
+template <typename ST, int MODE, bool FORCED>
+__global__ void __launch_bounds__(THREADS, MinBlocks<ST>::value)
+stream_collide_kernel(const __grid_constant__ StepParams p, const __grid_constant__ CUtensorMap tin,
+                      const __grid_constant__ CUtensorMap tout, const ST *__restrict__ fin)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    WarpCtx w;
+    warp_begin<ST>(w, smem);
+    bool abort = false;
+    for (int item = next_item(w, p.work); item < p.nitems; item = next_item(w, p.work)) {
+        if (!run_item<ST, MODE, FORCED>(w, p, &tin, &tout, fin, item % p.nstrips, item / p.nstrips, p.step)) {
+            abort = true;
+            break;
+        }
+    }
+    warp_end<ST>(w, abort, p.error, p.work);
+}
+
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(m) : "memory");
+}
+
+// One time step of every active domain of a batch.  Items run over the active
+// domains' (strip, segment) lists back to back; a warp finds its item's domain
+// by binary search in the prefix sums.  The forced or unforced collision is
+// chosen per domain, so a domain's arithmetic does not depend on which other
+// domains share the launch.
+template <typename ST, int MODE>
+__global__ void __launch_bounds__(THREADS, MinBlocks<ST>::value)
+stream_collide_batch_kernel(const __grid_constant__ BatchArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    WarpCtx w;
+    warp_begin<ST>(w, smem);
+    bool abort = false;
+    const int total = a.state->total_items;
+    const int n_active = a.state->n_active;
+    int last_slot = -1;
+    for (int item = next_item(w, a.work); item < total; item = next_item(w, a.work)) {
+        int lo = 0, hi = n_active;  // prefix[lo] <= item < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(a.prefix + mid) <= item) lo = mid;
+            else hi = mid;
+        }
+        const int slot = __ldg(a.active + lo);
+        const DomainDesc &D = a.domains[slot];
+        if (slot != last_slot) {
+            // the descriptors were written by host copies into global memory:
+            // acquire them for the tensor-map proxy before the first TMA use
+            tensormap_acquire(&D.tload[a.parity]);
+            tensormap_acquire(&D.tstore[a.parity ^ 1]);
+            last_slot = slot;
+        }
+        const int local = item - __ldg(a.prefix + lo);
+        const StepParams &p = D.p;
+        const ST *fin = static_cast<const ST *>(D.f[a.parity]);
+        const uint32_t step = __ldg(a.step0 + lo) + (uint32_t)a.k;
+        const bool ok = D.forced ? run_item<ST, MODE, true>(w, p, &D.tload[a.parity], &D.tstore[a.parity ^ 1], fin,
+                                                             local % p.nstrips, local / p.nstrips, step)
+                                 : run_item<ST, MODE, false>(w, p, &D.tload[a.parity], &D.tstore[a.parity ^ 1], fin,
+                                                              local % p.nstrips, local / p.nstrips, step);
+        if (!ok) {
+            abort = true;
+            break;
+        }
+    }
+    warp_end<ST>(w, abort, a.error, a.work);
+}
+
+template <typename ST>
+cudaError_t launch_batch_t(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s)
+{
+    using T = Tile<ST>;
+    switch (gi_mode) {
+    case LBM_GI_UNCORRECTED:
+        stream_collide_batch_kernel<ST, LBM_GI_UNCORRECTED><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
+        break;
+    case LBM_GI_CUBIC_ONLY:
+        stream_collide_batch_kernel<ST, LBM_GI_CUBIC_ONLY><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
+        break;
+    default: stream_collide_batch_kernel<ST, LBM_GI_FULL><<<grid, THREADS, T::SMEM_BYTES, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename ST, int MODE>
+int batch_blocks_variant()
+{
+    using T = Tile<ST>;
+    auto fn = stream_collide_batch_kernel<ST, MODE>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM_BYTES) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, THREADS, T::SMEM_BYTES) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+template <typename ST>
+int batch_blocks_t(int gi_mode)
+{
+    switch (gi_mode) {
+    case LBM_GI_UNCORRECTED: return batch_blocks_variant<ST, LBM_GI_UNCORRECTED>();
+    case LBM_GI_CUBIC_ONLY: return batch_blocks_variant<ST, LBM_GI_CUBIC_ONLY>();
+    default: return batch_blocks_variant<ST, LBM_GI_FULL>();
+    }
 }
 
 template <typename ST>

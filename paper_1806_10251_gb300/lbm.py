@@ -39,6 +39,22 @@ class Boundaries(ctypes.Structure):
                 ("solid", ctypes.c_void_p)]
 
 
+class Request(ctypes.Structure):
+    """lbm_request: one steady solve submitted to a batch."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nu", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("U", ctypes.c_double), ("bnd", Boundaries), ("use_bnd", ctypes.c_int), ("fx", ctypes.c_double),
+                ("fy", ctypes.c_double), ("tol", ctypes.c_double), ("max_steps", ctypes.c_long)]
+
+
+class Result(ctypes.Structure):
+    """lbm_result: state of a submitted request."""
+    _fields_ = [("state", ctypes.c_int), ("steps", ctypes.c_long), ("residual", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_CONVERGED, REQ_NOT_CONVERGED, REQ_DIVERGED, REQ_FAILED = range(6)
+
+
 class PopulationDesc(ctypes.Structure):
     """lbm_population_desc: a caller-owned device population array."""
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_int), ("storage", ctypes.c_int),
@@ -87,6 +103,17 @@ SIGNATURES = {
     "lbm_set_allocator": (ctypes.c_int, [ctypes.POINTER(Allocator)]),
     "lbm_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(_L)]),
     "lbm_residual_sums_noalloc": (ctypes.c_int, [ctypes.POINTER(PopulationDesc), _P, _P, _P, _P, _P]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    "lbm_batch_set_option": (ctypes.c_int, [_P, ctypes.c_char_p, _D]),
+    "lbm_batch_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(_L)]),
+    "lbm_batch_poll": (ctypes.c_int, [_P, _L, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]),
+    "lbm_batch_fields": (ctypes.c_int, [_P, _L, _P, _P, _P]),
+    "lbm_batch_release": (ctypes.c_int, [_P, _L]),
+    "lbm_batch_run": (ctypes.c_int, [_P, _D]),
+    "lbm_batch_start": (ctypes.c_int, [_P]),
+    "lbm_batch_stop": (ctypes.c_int, [_P]),
+    "lbm_batch_stats": (ctypes.c_int, [_P, _DP]),
+    "lbm_batch_destroy": (None, [_P]),
 }
 
 
@@ -299,6 +326,81 @@ def residual_sums_noalloc(desc: PopulationDesc, f_dev: int, snap_ux_dev: int, sn
     check(lib().lbm_residual_sums_noalloc(ctypes.byref(desc), ctypes.c_void_p(f_dev), ctypes.c_void_p(snap_ux_dev),
                                           ctypes.c_void_p(snap_uy_dev), ctypes.c_void_p(sums_dev),
                                           ctypes.c_void_p(stream) if stream else None))
+
+
+class Batch:
+    """A batch of steady solves (``lbm_batch``); methods map onto the C ABI."""
+
+    def __init__(self, hbm_budget_bytes: int, storage: int = STORAGE_F16, gi_mode: int = GI_FULL):
+        self._h = ctypes.c_void_p()
+        check(lib().lbm_batch_create(int(hbm_budget_bytes), int(storage), int(gi_mode), ctypes.byref(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().lbm_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key: str, value: float):
+        check(lib().lbm_batch_set_option(self._h, key.encode(), float(value)))
+
+    def submit(self, nx, ny, nu, gamma, U=0.0, sides=None, solid=None, fx=0.0, fy=0.0, tol=1e-6,
+               max_steps=1_000_000) -> int:
+        r = Request()
+        r.nx, r.ny, r.nu, r.gamma, r.U = int(nx), int(ny), float(nu), float(gamma), float(U)
+        keep = None
+        if sides is not None or solid is not None:
+            if sides is None:
+                sides = ((SIDE_WALL, 0, 0), (SIDE_WALL, 0, 0), (SIDE_WALL, 0, 0), (SIDE_MOVING_WALL, U, 0))
+            b, keep = make_boundaries(sides, solid)
+            r.bnd = b
+            r.use_bnd = 1
+        r.fx, r.fy, r.tol, r.max_steps = float(fx), float(fy), float(tol), int(max_steps)
+        rid = ctypes.c_long()
+        check(lib().lbm_batch_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
+        return rid.value
+
+    def submit_case(self, case, tol=1e-6, max_steps=1_000_000) -> int:
+        """Submit a ``workloads.Case``; a batch starts every domain at rest and
+        takes a uniform body force only."""
+        if case.force_x is not None or case.rho0 is not None or case.ux0 is not None:
+            raise ValueError("a batch request takes no force field and no initial fields")
+        return self.submit(case.nx, case.ny, case.nu, case.gamma, case.U, case.sides, case.solid, case.Fx,
+                           case.Fy, tol, max_steps)
+
+    def poll(self, rid: int):
+        done = ctypes.c_int()
+        res = Result()
+        check(lib().lbm_batch_poll(self._h, int(rid), ctypes.byref(done), ctypes.byref(res)))
+        return bool(done.value), res
+
+    def fields(self, rid: int, nx: int, ny: int):
+        out = [np.empty((ny, nx)) for _ in range(3)]
+        check(lib().lbm_batch_fields(self._h, int(rid), *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def release(self, rid: int):
+        check(lib().lbm_batch_release(self._h, int(rid)))
+
+    def run(self, wall_seconds: float = 0.0):
+        check(lib().lbm_batch_run(self._h, float(wall_seconds)))
+
+    def start(self):
+        check(lib().lbm_batch_start(self._h))
+
+    def stop(self):
+        check(lib().lbm_batch_stop(self._h))
+
+    def stats(self) -> dict:
+        a = (ctypes.c_double * 6)()
+        check(lib().lbm_batch_stats(self._h, a))
+        return {"cell_updates": a[0], "launches": int(a[1]), "ticks": int(a[2]), "running": int(a[3]),
+                "queued": int(a[4]), "device_bytes": int(a[5])}
 
 
 def solver_from_case(case, gi_mode: int = GI_FULL, storage: int = STORAGE_F32, **options) -> Solver:
