@@ -133,7 +133,7 @@ StepParams make_params(const lbm_ctx *c)
     p.work = c->d_work;
     p.cf.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
     p.cd.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
-    p.nstrips = (c->nx + WS - 1) / WS;
+    p.nstrips = (c->nx + strip_width(c->storage) - 1) / strip_width(c->storage);
     int bps = 1;
     switch (c->storage) {
     case LBM_STORAGE_F16: bps = blocks_per_sm_f16(c->gi_mode); break;
@@ -179,11 +179,12 @@ cudaError_t launch_step(const lbm_ctx *c, const StepParams &p, int grid)
     const CUtensorMap &tin = c->tload[c->cur];
     const CUtensorMap &tout = c->tstore[1 - c->cur];
     const void *fin = c->f[c->cur];
+    void *fout = c->f[1 - c->cur];
     switch (c->storage) {
-    case LBM_STORAGE_F16: return launch_step_f16(p, tin, tout, fin, grid, c->stream);
-    case LBM_STORAGE_BF16: return launch_step_bf16(p, tin, tout, fin, grid, c->stream);
-    case LBM_STORAGE_F64: return launch_step_f64(p, tin, tout, fin, grid, c->stream);
-    default: return launch_step_f32(p, tin, tout, fin, grid, c->stream);
+    case LBM_STORAGE_F16: return launch_step_f16(p, tin, tout, fin, fout, grid, c->stream);
+    case LBM_STORAGE_BF16: return launch_step_bf16(p, tin, tout, fin, fout, grid, c->stream);
+    case LBM_STORAGE_F64: return launch_step_f64(p, tin, tout, fin, fout, grid, c->stream);
+    default: return launch_step_f32(p, tin, tout, fin, fout, grid, c->stream);
     }
 }
 

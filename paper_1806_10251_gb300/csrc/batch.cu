@@ -155,9 +155,9 @@ void free_slot(Slot &s)
     s = Slot();
 }
 
-void set_geometry(StepParams &p, int Ly)
+void set_geometry(StepParams &p, int Ly, int storage)
 {
-    p.nstrips = (p.nx + WS - 1) / WS;
+    p.nstrips = (p.nx + strip_width(storage) - 1) / strip_width(storage);
     p.Ly = Ly < p.ny ? Ly : p.ny;
     p.nitems = p.nstrips * ((p.ny + p.Ly - 1) / p.Ly);
 }
@@ -232,7 +232,7 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     p.sround = b->sround;
     p.cf.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
     p.cd.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
-    set_geometry(p, b->Ly);
+    set_geometry(p, b->Ly, b->storage);
     s.tol = r.tol;
     s.max_steps = r.max_steps;
     s.res_blocks = residual_blocks(p);
@@ -358,7 +358,7 @@ void apply_Ly(lbm_batch *b, int Ly)
         for (int k = 0; k < b->max_slots; ++k) {
             Slot &s = b->slots[k];
             if (!s.used || !s.running) continue;
-            set_geometry(s.p, Ly);
+            set_geometry(s.p, Ly, b->storage);
             b->h_desc[k].p = s.p;
             cudaMemcpyAsync(&b->d_desc[k].p, &b->h_desc[k].p, sizeof(StepParams), cudaMemcpyHostToDevice,
                             b->stream);

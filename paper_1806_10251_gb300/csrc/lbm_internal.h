@@ -13,9 +13,13 @@ namespace lbm {
 
 // Columns of one warp strip of the stream-collide kernel (one per lane), warps
 // per block.
-constexpr int WS = 32;
+constexpr int WS = 32;  // one cell per lane (FP64 storage)
 constexpr int WARPS = 4;
 constexpr int THREADS = 32 * WARPS;  // threads per block of the step kernel
+
+// Columns of a warp strip for a storage type: the FP32/FP16/BF16 kernels give a
+// lane two neighbouring cells (packed FP32 arithmetic), the FP64 kernel one.
+inline int strip_width(int storage) { return storage == LBM_STORAGE_F64 ? WS : 2 * WS; }
 
 // FP16 storage holds 2^14 g rather than g (an exact power-of-two scale): the
 // deviations of slow regions (|g| down to about 1e-8) then stay in the normal
@@ -127,18 +131,18 @@ struct BatchArgs {
 // The launchers below are defined per storage type (one translation unit each).
 // tin: TMA descriptor of fin for loads (box: one row of all planes of a warp
 // strip plus halo); tout: descriptor of fout for stores (box: one strip row).
-cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
-cudaError_t launch_step_f16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
-cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
-cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, int grid, cudaStream_t s);
+cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
+cudaError_t launch_step_f16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
+cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
+cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
 cudaError_t launch_batch_step(int storage, int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
 int batch_blocks_per_sm(int storage, int gi_mode);
 int blocks_per_sm_f32(int gi_mode);
 int blocks_per_sm_f16(int gi_mode);
 int blocks_per_sm_bf16(int gi_mode);
 int blocks_per_sm_f64(int gi_mode);
-// Encode the TMA descriptors of a population buffer: load box {WS + 2 PAD, 1, 9}
-// and store box {WS, 1, 9}.
+// Encode the TMA descriptors of a population buffer: load box {W + 2 PAD, 1, 9}
+// with W the strip width of the storage type, and store box {WS, 1, 9}.
 cudaError_t make_tensor_maps(CUtensorMap *load, CUtensorMap *store, int storage, void *base, int nx, int ny,
                              int pitch, long long plane);
 

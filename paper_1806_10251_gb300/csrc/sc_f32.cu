@@ -1,21 +1,21 @@
-// Step kernel instantiations for the float population storage.
-#include "stream_collide.cuh"
+// Step kernel instantiations for the float population storage (two cells per lane).
+#include "stream_collide_x2.cuh"
 
 namespace lbm {
 
-cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin,
-                           int grid, cudaStream_t s)
+cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &, const void *fin,
+                           void *fout, int grid, cudaStream_t s)
 {
-    return launch_step_t<float>(p, tin, tout, fin, grid, s);
+    return launch_step_x2_t<float>(p, tin, fin, fout, grid, s);
 }
 
 cudaError_t launch_batch_f32(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s)
 {
-    return launch_batch_t<float>(gi_mode, a, grid, s);
+    return launch_batch_x2_t<float>(gi_mode, a, grid, s);
 }
 
-int batch_blocks_f32(int gi_mode) { return batch_blocks_t<float>(gi_mode); }
+int batch_blocks_f32(int gi_mode) { return batch_blocks_x2_t<float>(gi_mode); }
 
-int blocks_per_sm_f32(int gi_mode) { return blocks_per_sm_t<float>(gi_mode); }
+int blocks_per_sm_f32(int gi_mode) { return blocks_per_sm_x2_t<float>(gi_mode); }
 
 }  // namespace lbm

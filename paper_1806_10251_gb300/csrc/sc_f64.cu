@@ -4,7 +4,7 @@
 namespace lbm {
 
 cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin,
-                           int grid, cudaStream_t s)
+                           void *, int grid, cudaStream_t s)
 {
     return launch_step_t<double>(p, tin, tout, fin, grid, s);
 }

@@ -2,7 +2,7 @@
 // box is one row of all nine planes plus the halo columns of a strip.
 #include <cudaTypedefs.h>
 
-#include "stream_collide.cuh"
+#include "stream_collide_x2.cuh"
 
 namespace lbm {
 
@@ -43,7 +43,10 @@ template <typename ST>
 cudaError_t encode_pair(CUtensorMap *load, CUtensorMap *store, CUtensorMapDataType dtype, void *base, int nx, int ny,
                         int pitch, long long plane)
 {
-    cudaError_t e = encode<ST>(load, dtype, base, nx, ny, pitch, plane, Tile<ST>::BWX);
+    // load box of the storage type's step kernel: 64-column strips (two cells
+    // per lane) for FP32/FP16/BF16, 32-column strips for FP64
+    const int box = sizeof(ST) == 8 ? Tile<ST>::BWX : Tile2<ST>::BWX;
+    cudaError_t e = encode<ST>(load, dtype, base, nx, ny, pitch, plane, box);
     if (e != cudaSuccess) return e;
     return encode<ST>(store, dtype, base, nx, ny, pitch, plane, WS);
 }
