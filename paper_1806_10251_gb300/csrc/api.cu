@@ -98,6 +98,18 @@ namespace {
 
 size_t pop_bytes(const lbm_ctx *c) { return (size_t)9 * (size_t)c->plane * storage_bytes(c->storage); }
 
+// Resident blocks per SM of the step-kernel variant p launches.
+int step_blocks_per_sm(const lbm_ctx *c, const StepParams &p)
+{
+    const bool forced = p.force != nullptr || p.Fx != 0.0 || p.Fy != 0.0;
+    switch (c->storage) {
+    case LBM_STORAGE_F16: return blocks_per_sm_f16(c->gi_mode, forced);
+    case LBM_STORAGE_BF16: return blocks_per_sm_bf16(c->gi_mode, forced);
+    case LBM_STORAGE_F64: return blocks_per_sm_f64(c->gi_mode, forced);
+    default: return blocks_per_sm_f32(c->gi_mode, forced);
+    }
+}
+
 StepParams make_params(const lbm_ctx *c)
 {
     StepParams p;
@@ -133,14 +145,9 @@ StepParams make_params(const lbm_ctx *c)
     p.work = c->d_work;
     p.cf.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
     p.cd.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
+    p.c2.set(p.cf);
     p.nstrips = (c->nx + strip_width(c->storage) - 1) / strip_width(c->storage);
-    int bps = 1;
-    switch (c->storage) {
-    case LBM_STORAGE_F16: bps = blocks_per_sm_f16(c->gi_mode); break;
-    case LBM_STORAGE_BF16: bps = blocks_per_sm_bf16(c->gi_mode); break;
-    case LBM_STORAGE_F64: bps = blocks_per_sm_f64(c->gi_mode); break;
-    default: bps = blocks_per_sm_f32(c->gi_mode); break;
-    }
+    const int bps = step_blocks_per_sm(c, p);
     const int resident = c->num_sms * bps * WARPS;  // resident warps
     int Ly = c->Ly_option;
     if (Ly <= 0) {
@@ -162,13 +169,7 @@ StepParams make_params(const lbm_ctx *c)
 
 int step_grid(const lbm_ctx *c, const StepParams &p)
 {
-    int bps = 1;
-    switch (c->storage) {
-    case LBM_STORAGE_F16: bps = blocks_per_sm_f16(c->gi_mode); break;
-    case LBM_STORAGE_BF16: bps = blocks_per_sm_bf16(c->gi_mode); break;
-    case LBM_STORAGE_F64: bps = blocks_per_sm_f64(c->gi_mode); break;
-    default: bps = blocks_per_sm_f32(c->gi_mode); break;
-    }
+    const int bps = step_blocks_per_sm(c, p);
     const int resident = c->num_sms * bps;
     const int blocks = (p.nitems + WARPS - 1) / WARPS;
     return blocks < resident ? blocks : resident;

@@ -232,6 +232,7 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     p.sround = b->sround;
     p.cf.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
     p.cd.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
+    p.c2.set(p.cf);
     set_geometry(p, b->Ly, b->storage);
     s.tol = r.tol;
     s.max_steps = r.max_steps;

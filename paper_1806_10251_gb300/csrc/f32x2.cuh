@@ -69,12 +69,12 @@ __device__ __forceinline__ float rcp_nr(float x)
     const float e = fmaf(-x, r, 1.0f);
     return fmaf(r, e, r);
 }
-__device__ __forceinline__ F2 recip2(F2 x)
+__device__ __forceinline__ F2 recip2(F2 x, F2 one)
 {
     F2 r{0.f, 0.f};
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(x.x));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(x.y));
-    const F2 e = fnma2(x, r, f2(1.0f));
+    const F2 e = fnma2(x, r, one);
     return fma2(r, e, r);
 }
 

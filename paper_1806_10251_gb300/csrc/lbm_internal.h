@@ -70,6 +70,52 @@ struct Consts {
     }
 };
 
+// The collision constants of the packed-FP32 kernel (two cells per lane), each
+// duplicated into a pair, so that a packed instruction reads the pair as one
+// operand instead of the kernel building it from a scalar.
+struct Consts2 {
+    float2 one, half, two, three, four, m_two, third, two_thirds, ninth;
+    float2 ig, half_ig, ig2;
+    float2 w3_12, w4_4, w5_4, w6_4, w7_4, w8_4, c6;
+    float2 hA, hB, B, C3, a3, a4, k3x2, k4x2, mk5;  // -A/2, -B/2, B, C/3, a3, a4, 2 k3, 2 k4, -k5
+    float2 Fx, Fy;
+
+    void set(const Consts<float> &c)
+    {
+        auto p = [](float v) { return make_float2(v, v); };
+        one = p(1.f);
+        half = p(0.5f);
+        two = p(2.f);
+        three = p(3.f);
+        four = p(4.f);
+        m_two = p(-2.f);
+        third = p(1.f / 3.f);
+        two_thirds = p(2.f / 3.f);
+        ninth = p(1.f / 9.f);
+        ig = p(c.ig);
+        half_ig = p(c.half_ig);
+        ig2 = p(c.ig2);
+        w3_12 = p(c.w3_12);
+        w4_4 = p(c.w4_4);
+        w5_4 = p(c.w5_4);
+        w6_4 = p(c.w6_4);
+        w7_4 = p(c.w7_4);
+        w8_4 = p(c.w8_4);
+        c6 = p(c.c6);
+        hA = p(-0.5f * c.A);
+        hB = p(-0.5f * c.B);
+        B = p(c.B);
+        C3 = p(c.C3);
+        a3 = p(c.a3);
+        a4 = p(c.a4);
+        k3x2 = p(2.f * c.k3);
+        k4x2 = p(2.f * c.k4);
+        mk5 = p(-c.k5);
+        Fx = p(c.Fx);
+        Fy = p(c.Fy);
+    }
+};
+
 // Everything one launch of the step kernel needs, passed by value.
 struct StepParams {
     int nx, ny;
@@ -98,6 +144,7 @@ struct StepParams {
     unsigned int step;       // step index of this launch (low 32 bits), single-domain kernel
     Consts<float> cf;
     Consts<double> cd;
+    Consts2 c2;
 };
 
 // One domain of a batch, in device memory (TMA descriptors need 64-byte alignment).
@@ -137,10 +184,10 @@ cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const 
 cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
 cudaError_t launch_batch_step(int storage, int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
 int batch_blocks_per_sm(int storage, int gi_mode);
-int blocks_per_sm_f32(int gi_mode);
-int blocks_per_sm_f16(int gi_mode);
-int blocks_per_sm_bf16(int gi_mode);
-int blocks_per_sm_f64(int gi_mode);
+int blocks_per_sm_f32(int gi_mode, bool forced);
+int blocks_per_sm_f16(int gi_mode, bool forced);
+int blocks_per_sm_bf16(int gi_mode, bool forced);
+int blocks_per_sm_f64(int gi_mode, bool forced);
 // Encode the TMA descriptors of a population buffer: load box {W + 2 PAD, 1, 9}
 // with W the strip width of the storage type, and store box {WS, 1, 9}.
 cudaError_t make_tensor_maps(CUtensorMap *load, CUtensorMap *store, int storage, void *base, int nx, int ny,

@@ -16,6 +16,6 @@ cudaError_t launch_batch_f16(int gi_mode, const BatchArgs &a, int grid, cudaStre
 
 int batch_blocks_f16(int gi_mode) { return batch_blocks_x2_t<__half>(gi_mode); }
 
-int blocks_per_sm_f16(int gi_mode) { return blocks_per_sm_x2_t<__half>(gi_mode); }
+int blocks_per_sm_f16(int gi_mode, bool forced) { return blocks_per_sm_x2_t<__half>(gi_mode, forced); }
 
 }  // namespace lbm

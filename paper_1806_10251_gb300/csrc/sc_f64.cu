@@ -16,6 +16,6 @@ cudaError_t launch_batch_f64(int gi_mode, const BatchArgs &a, int grid, cudaStre
 
 int batch_blocks_f64(int gi_mode) { return batch_blocks_t<double>(gi_mode); }
 
-int blocks_per_sm_f64(int gi_mode) { return blocks_per_sm_t<double>(gi_mode); }
+int blocks_per_sm_f64(int gi_mode, bool forced) { return blocks_per_sm_t<double>(gi_mode, forced); }
 
 }  // namespace lbm

@@ -712,23 +712,21 @@ int blocks_per_sm_variant()
     return n > 0 ? n : 1;
 }
 
-// Both force variants get the dynamic shared-memory attribute; the smaller
-// occupancy of the two is returned.
+// Resident blocks per SM of the variant a launch with these settings uses (its
+// dynamic shared-memory attribute is set on the way).
 template <typename ST, int MODE>
-int blocks_per_sm_mode()
+int blocks_per_sm_mode(bool forced)
 {
-    const int a = blocks_per_sm_variant<ST, MODE, false>();
-    const int b = blocks_per_sm_variant<ST, MODE, true>();
-    return a < b ? a : b;
+    return forced ? blocks_per_sm_variant<ST, MODE, true>() : blocks_per_sm_variant<ST, MODE, false>();
 }
 
 template <typename ST>
-int blocks_per_sm_t(int gi_mode)
+int blocks_per_sm_t(int gi_mode, bool forced)
 {
     switch (gi_mode) {
-    case LBM_GI_UNCORRECTED: return blocks_per_sm_mode<ST, LBM_GI_UNCORRECTED>();
-    case LBM_GI_CUBIC_ONLY: return blocks_per_sm_mode<ST, LBM_GI_CUBIC_ONLY>();
-    default: return blocks_per_sm_mode<ST, LBM_GI_FULL>();
+    case LBM_GI_UNCORRECTED: return blocks_per_sm_mode<ST, LBM_GI_UNCORRECTED>(forced);
+    case LBM_GI_CUBIC_ONLY: return blocks_per_sm_mode<ST, LBM_GI_CUBIC_ONLY>(forced);
+    default: return blocks_per_sm_mode<ST, LBM_GI_FULL>(forced);
     }
 }
 

@@ -29,14 +29,20 @@ struct Tile2 {
     static constexpr int BWX = SW + 2 * PAD;      // load box width (columns)
     static constexpr int ROW_BYTES = 9 * BWX * ES;
     static constexpr int SLOT_BYTES = (ROW_BYTES + 127) / 128 * 128;
-    static constexpr int NSLOT = ES == 4 ? 6 : 8;  // ring depth (3 rows are read at a time)
+    // ring depth (3 rows are read at a time; a power of two keeps the slot
+    // arithmetic to a mask)
+    static constexpr int NSLOT = ES == 4 ? 4 : 8;
     static constexpr int BAR_OFF = NSLOT * SLOT_BYTES;
     static constexpr int WARP_BYTES = (BAR_OFF + NSLOT * 8 + 127) / 128 * 128;
     static constexpr int SMEM_BYTES = WARPS * WARP_BYTES;
 };
 
-// Resident blocks per SM the register budget is sized for.
-constexpr int MIN_BLOCKS_X2 = 3;
+// Resident blocks per SM the register budget is sized for: four (16 warps) for
+// the unforced single-domain kernel; three for the forced one (the source
+// terms) and for the batch kernel, whose per-domain parameters live in global
+// memory and hold more registers.
+constexpr int MIN_BLOCKS_X2 = 4;
+constexpr int MIN_BLOCKS_BATCH_X2 = 3;
 
 // Pairs of stored values <-> F2 (storage scale and rounding as StorageTraits).
 template <typename ST> struct PairIO;
@@ -462,8 +468,8 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         }
         F2 Fx = f2(0.f), Fy = f2(0.f);
         if (FORCED) {
-            Fx = f2(c.Fx);
-            Fy = f2(c.Fy);
+            Fx = ld(p.c2.Fx);
+            Fy = ld(p.c2.Fy);
             if (p.force) {
                 const size_t i = (size_t)y * p.pitch + xe;
                 const float2 fx2 = __ldg(reinterpret_cast<const float2 *>(p.force + i));
@@ -475,8 +481,8 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         F2 out[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) out[a] = cur[a];
-        const F2 half = f2(0.5f);
-        collide_x2<MODE, FORCED>(out, half * (re - rw), half * (rn - rs), Fx, Fy, c, p.guard != 0, p.guard_count);
+        const F2 half = ld(p.c2.half);
+        collide_x2<MODE, FORCED>(out, half * (re - rw), half * (rn - rs), Fx, Fy, p.c2, p.guard != 0, p.guard_count);
         if (!FAST && cur_valid != 3) {
 #pragma unroll
             for (int k = 0; k < 2; ++k)
@@ -524,7 +530,7 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
 
 // One time step of one domain.
 template <typename ST, int MODE, bool FORCED>
-__global__ void __launch_bounds__(THREADS, MIN_BLOCKS_X2)
+__global__ void __launch_bounds__(THREADS, FORCED ? MIN_BLOCKS_BATCH_X2 : MIN_BLOCKS_X2)
 stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_constant__ CUtensorMap tin,
                          const ST *__restrict__ fin, ST *__restrict__ fout)
 {
@@ -543,7 +549,7 @@ stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_cons
 
 // One time step of every active domain of a batch (see stream_collide_batch_kernel).
 template <typename ST, int MODE>
-__global__ void __launch_bounds__(THREADS, MIN_BLOCKS_X2)
+__global__ void __launch_bounds__(THREADS, MIN_BLOCKS_BATCH_X2)
 stream_collide_x2_batch_kernel(const __grid_constant__ BatchArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -627,22 +633,22 @@ int occupancy_of(KernelFn fn, int smem)
     return n > 0 ? n : 1;
 }
 
-// Resident blocks per SM of the step kernel (the forced and unforced variants
-// are both prepared; the smaller count is returned).
+// Resident blocks per SM of the step-kernel variant a launch with these
+// settings uses (its dynamic shared-memory attribute is set on the way).
 template <typename ST>
-int blocks_per_sm_x2_t(int gi_mode)
+int blocks_per_sm_x2_t(int gi_mode, bool forced)
 {
     using T = Tile2<ST>;
     switch (gi_mode) {
     case LBM_GI_UNCORRECTED:
-        return min(occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_UNCORRECTED, false>, T::SMEM_BYTES),
-                   occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_UNCORRECTED, true>, T::SMEM_BYTES));
+        return forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_UNCORRECTED, true>, T::SMEM_BYTES)
+                      : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_UNCORRECTED, false>, T::SMEM_BYTES);
     case LBM_GI_CUBIC_ONLY:
-        return min(occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, false>, T::SMEM_BYTES),
-                   occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, true>, T::SMEM_BYTES));
+        return forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, true>, T::SMEM_BYTES)
+                      : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, false>, T::SMEM_BYTES);
     default:
-        return min(occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false>, T::SMEM_BYTES),
-                   occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true>, T::SMEM_BYTES));
+        return forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true>, T::SMEM_BYTES)
+                      : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false>, T::SMEM_BYTES);
     }
 }
 
