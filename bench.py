@@ -30,7 +30,10 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and steady-state solves/sec (FP16-storage batched vs plain FP32) at L2≤1e-3"
 BYTES_PER_CELL = {"f32": 72, "f16": 36, "bf16": 36, "f64": 144}
 STORAGE_CODE = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3}
-KERNEL_SOURCES = ["paper_1806_10251_gb300/csrc/stream_collide.cuh",
+KERNEL_SOURCES = ["paper_1806_10251_gb300/csrc/stream_collide_x2.cuh",
+                  "paper_1806_10251_gb300/csrc/collide_x2.cuh",
+                  "paper_1806_10251_gb300/csrc/f32x2.cuh",
+                  "paper_1806_10251_gb300/csrc/stream_collide.cuh",
                   "paper_1806_10251_gb300/csrc/d2q9_collide.cuh"]
 
 
@@ -49,6 +52,20 @@ def parse():
     ap.add_argument("--e2e-check-every", type=int, default=100)
     ap.add_argument("--cells-per-item", type=int, default=0,
                     help="rows per work item of the step kernel (0 = automatic)")
+    ap.add_argument("--workload", choices=["cavity", "batch", "serve"], default="cavity",
+                    help="cavity: the timed step of one large domain (default); batch: steady solves/s of "
+                         "independent cavities, FP16 batch against the plain FP32 solver one domain at a time; "
+                         "serve: a Poisson stream of steady-solve requests into the batch engine")
+    ap.add_argument("--batch-count", type=int, default=256, help="batch: first N cavities of the seeded set")
+    ap.add_argument("--tol", type=float, default=1e-3, help="batch/serve: steady when r < tol between checks")
+    ap.add_argument("--check-every", type=int, default=1000)
+    ap.add_argument("--max-steps", type=int, default=400000)
+    ap.add_argument("--accuracy-sample", type=int, default=6,
+                    help="batch: smallest domains whose results are compared with a converged FP32 solve")
+    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
+    ap.add_argument("--side-min", type=int, default=128)
+    ap.add_argument("--side-max", type=int, default=512)
     return ap.parse_args()
 
 
@@ -194,11 +211,171 @@ def run_reference(args, world, rank):
     return 0
 
 
+def rel_l2(u, v, uo, vo, mask=None):
+    import numpy as np
+    if mask is None:
+        mask = np.ones(u.shape, bool)
+    d = ((u - uo) ** 2 + (v - vo) ** 2)[mask].sum()
+    n = (uo ** 2 + vo ** 2)[mask].sum()
+    return float(np.sqrt(d / n))
+
+
+def run_batch(args, rank):
+    """Steady solves per second: the seeded set of independent cavities (sides
+    64 + 32k, k ~ U{0..30}; Re ~ U[100, 1000]; gamma ~ U[0.2, 1.0]; U = 0.1),
+    solved (a) by the plain FP32 path one domain at a time (lbm_run_to_steady:
+    one launch per step, no graph) and (b) as one FP16 batch (lbm_batch_*: all
+    domains in lockstep under a captured CUDA graph).  Both stop a domain at the
+    first check where r < tol.  The smallest domains of the set are then solved
+    to the FP32 floor (r < 2e-7) as the reference for both arms' L2 errors."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1806_10251_gb300 import lbm
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    cases = wl.batch_cavities(256, seed=0)[: args.batch_count]
+    K, tol, mx = args.check_every, args.tol, args.max_steps
+    cells = sum(c.cells for c in cases)
+    # (a) plain FP32, sequential
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_a, fields_a = [], {}
+    order = sorted(range(len(cases)), key=lambda i: cases[i].cells)
+    sample = set(order[: args.accuracy_sample])
+    for i, c in enumerate(cases):
+        g = lbm.Solver(c.nx, c.ny, c.nu, c.gamma, c.U)
+        st, steps, r = g.run_to_steady(tol, K, mx, raise_on_error=False)
+        res_a.append((st, steps, r))
+        if i in sample:
+            fields_a[i] = g.fields()[1:]
+        g.close()
+    t_a = time.perf_counter() - t0
+    steps_a = sum(x[1] for x in res_a)
+    upd_a = sum(c.cells * x[1] for c, x in zip(cases, res_a))
+    # (b) FP16 batch
+    b = lbm.Batch(64 << 30, storage=lbm.STORAGE_F16)
+    b.set_option("check_every", K)
+    t0 = time.perf_counter()
+    ids = [b.submit_case(c, tol=tol, max_steps=mx) for c in cases]
+    b.run()
+    t_b = time.perf_counter() - t0
+    res_b = [b.poll(i)[1] for i in ids]
+    stats = b.stats()
+    fields_b = {i: b.fields(ids[i], cases[i].nx, cases[i].ny)[1:] for i in sample}
+    b.close()
+    # accuracy on the sample: both arms against FP32 driven to its floor
+    acc = []
+    for i in sorted(sample):
+        c = cases[i]
+        g = lbm.Solver(c.nx, c.ny, c.nu, c.gamma, c.U)
+        st, steps, r = g.run_to_steady(2e-7, K, 2_000_000, raise_on_error=False)
+        _, uo, vo = g.fields()
+        g.close()
+        acc.append({"side": c.nx, "Re": round(c.meta["Re"], 1), "gamma": round(c.gamma, 3),
+                    "ref_steps": steps, "ref_residual": r,
+                    "l2_fp16_batch": rel_l2(*fields_b[i], uo, vo), "l2_fp32_plain": rel_l2(*fields_a[i], uo, vo)})
+    conv_a = sum(1 for x in res_a if x[0] == 0)
+    conv_b = sum(1 for x in res_b if x.state == lbm.REQ_CONVERGED)
+    line = {"metric": "steady solves/s (FP16 batch vs plain FP32)", "workload": "batch",
+            "value": len(cases) / t_b, "unit": "solves/s", "higher_is_better": True,
+            "plain_fp32": {"value": len(cases) / t_a, "seconds": t_a, "converged": conv_a, "steps": steps_a,
+                           "mlups": upd_a / t_a / 1e6},
+            "fp16_batch": {"value": len(cases) / t_b, "seconds": t_b, "converged": conv_b,
+                           "steps": sum(x.steps for x in res_b), "launches": stats["launches"],
+                           "mlups": stats["cell_updates"] / t_b / 1e6},
+            "speedup": t_a / t_b,
+            "config": {"domains": len(cases), "cells": cells, "tol": tol, "check_every": K, "max_steps": mx,
+                       "set": "batch_cavities(256, seed=0)" + (f"[:{len(cases)}]" if len(cases) < 256 else ""),
+                       "gi_mode": "full", "storage_b": "f16 (stochastic rounding)", "storage_a": "f32"},
+            "accuracy_sample": acc, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args, rank):
+    """Serving: a Poisson stream of steady-solve requests (cavity or obstacle
+    channel, p = 1/2; side on multiples of 32 in [side-min, side-max]; Re ~
+    U[50, 1000]; gamma ~ U[0.2, 1.0]; FP16 storage) submitted at their arrival
+    times to the batch engine running on a background thread (continuous
+    batching: admission by device footprint as memory frees up).  Reports the
+    arrival-to-steady latency percentiles, the aggregate MLUPS and the queue."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1806_10251_gb300 import lbm
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    reqs = wl.poisson_requests(count=args.requests, rate=args.rate, seed=0, side_min=args.side_min,
+                               side_max=args.side_max)
+    budget = 24 << 30
+    b = lbm.Batch(budget, storage=lbm.STORAGE_F16)
+    b.set_option("check_every", args.check_every)
+    b.start()
+    t0 = time.perf_counter()
+    ids, pending, done = [], set(), {}
+    depth = []
+    for ta, c in reqs:
+        while True:
+            now = time.perf_counter() - t0
+            if now >= ta:
+                break
+            for rid in list(pending):
+                fin, res = b.poll(rid)
+                if fin:
+                    done[rid] = res
+                    pending.discard(rid)
+                    b.release(rid)
+            time.sleep(min(0.002, ta - now))
+        rid = b.submit_case(c, tol=args.tol, max_steps=args.max_steps)
+        ids.append(rid)
+        pending.add(rid)
+        st = b.stats()
+        depth.append((st["running"], st["queued"]))
+    while pending:
+        for rid in list(pending):
+            fin, res = b.poll(rid)
+            if fin:
+                done[rid] = res
+                pending.discard(rid)
+                b.release(rid)
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    stats = b.stats()
+    b.stop()
+    b.close()
+    lat = np.array([done[i].t_done - done[i].t_submit for i in ids])
+    queue = np.array([done[i].t_admit - done[i].t_submit for i in ids])
+    line = {"metric": "arrival-to-steady latency and aggregate MLUPS (serving, FP16 batch engine)",
+            "workload": "serve", "value": float(np.percentile(lat, 50)), "unit": "s (p50 latency)",
+            "higher_is_better": False,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "queue_wait_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+            "aggregate_mlups": stats["cell_updates"] / wall / 1e6, "wall_s": wall,
+            "max_running": int(max(d[0] for d in depth)), "max_queued": int(max(d[1] for d in depth)),
+            "converged": int(sum(done[i].state == lbm.REQ_CONVERGED for i in ids)), "requests": len(ids),
+            "config": {"rate_per_s": args.rate, "requests": args.requests, "side": [args.side_min, args.side_max],
+                       "tol": args.tol, "check_every": args.check_every, "budget_bytes": budget,
+                       "stream": "poisson_requests(seed=0)"},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload == "batch":
+        return run_batch(args, rank)
+    if args.workload == "serve":
+        return run_serve(args, rank)
 
     import numpy as np
     import torch
@@ -324,7 +501,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": profiled_traffic(args.storage, args.n),
-                         "bytes_per_cell": bpc, "kernel": "stream_collide_kernel"},
+                         "bytes_per_cell": bpc,
+                         "kernel": "stream_collide_kernel" if args.storage == "f64" else "stream_collide_x2_kernel"},
             "gpu_launches": launches,
             "e2e": e2e,
             "clocks": clk,

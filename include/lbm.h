@@ -196,8 +196,9 @@ typedef struct {
 /* storage: LBM_STORAGE_*; gi_mode: LBM_GI_*; hbm_budget_bytes bounds the sum of
  * the admitted requests' footprints (2 population buffers + residual snapshot
  * + mask).  Options: "check_every" (K, even, default 1000: steps between
- * convergence checks, one CUDA graph of K launches), "rows_per_item" (0 =
- * autotune on the first admitted set), "stochastic_rounding" (as lbm_set_option,
+ * convergence checks, one CUDA graph of K launches), "rows_per_item" (rows of
+ * a warp's work item; 0 = chosen by timing a few steps whenever the running
+ * work has changed by more than 2x), "stochastic_rounding" (as lbm_set_option,
  * default 1, for domains admitted afterwards).  The error status of create is
  * LBM_ERR_INVALID for bad arguments, LBM_ERR_CUDA without a device, LBM_ERR_OOM
  * when the batch's own tables cannot be allocated.  A request is initialised at

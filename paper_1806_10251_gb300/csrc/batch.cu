@@ -98,6 +98,7 @@ struct lbm_batch {
     int Ly_option = 0;
     int Ly = 24;
     bool tuned = false;
+    double tuned_strip_rows = 0;  // active strip-rows when the rows per item were last chosen
     int parity = 0;
     int num_sms = 1;
     std::vector<Slot> slots;
@@ -368,18 +369,45 @@ void apply_Ly(lbm_batch *b, int Ly)
     cudaStreamSynchronize(b->stream);
 }
 
-// Pick the rows per item (the tile height of a warp's work item) by timing a
-// few steps of the current batch for each candidate.  The steps taken count.
+// Strip-rows of the running domains (one warp-strip row is the unit of work
+// of the step kernel).
+double active_strip_rows(lbm_batch *b)
+{
+    std::lock_guard<std::mutex> lk(b->mu);
+    double n = 0;
+    const int w = strip_width(b->storage);
+    for (int k = 0; k < b->max_slots; ++k) {
+        const Slot &s = b->slots[k];
+        if (s.used && s.running) n += (double)((s.nx + w - 1) / w) * s.ny;
+    }
+    return n;
+}
+
+// Pick the rows per item (the tile height of a warp's work item).  A warp
+// works through its item's rows one after another, so the item height bounds
+// the latency of a launch when there is little work, while short items re-read
+// more halo rows when there is much.  The starting point gives about four
+// items per resident warp over the whole active set (1..24 rows); the
+// candidates h/2, h, 2h are then timed on a few steps of the current batch
+// (the steps count) and the fastest kept.  Chosen again whenever the active
+// work has changed by more than a factor of two.
 lbm_status autotune(lbm_batch *b)
 {
-    const int cand[5] = {8, 12, 16, 24, 32};
+    const double rows = active_strip_rows(b);
+    const int resident = b->num_sms * batch_blocks_per_sm(b->storage, b->gi_mode) * WARPS;
+    int h = (int)ceil(rows / (4.0 * resident));
+    h = h < 1 ? 1 : (h > 24 ? 24 : h);
+    int cand[3] = {h > 1 ? (h + 1) / 2 : 1, h, h < 24 ? 2 * h : 32};
     float best_ms = 1e30f;
-    int best = b->Ly;
+    int best = h;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LBM_ERR_CUDA;
     const int reps = 4;  // even: the parity is unchanged
     const int grid = batch_grid(b);
+    int last = -1;
     for (int c : cand) {
+        if (c == last) continue;
+        last = c;
         apply_Ly(b, c);
         double cells;
         build_active(b, cells);
@@ -408,6 +436,7 @@ lbm_status autotune(lbm_batch *b)
     cudaEventDestroy(e1);
     apply_Ly(b, best);
     b->tuned = true;
+    b->tuned_strip_rows = rows;
     return LBM_OK;
 }
 
@@ -443,6 +472,10 @@ lbm_status tick(lbm_batch *b, bool *busy)
     int n = build_active(b, cells);
     *busy = n > 0;
     if (n == 0) return LBM_OK;
+    if (b->Ly_option <= 0) {
+        const double rows = active_strip_rows(b);
+        if (!b->tuned || rows > 2.0 * b->tuned_strip_rows || rows < 0.5 * b->tuned_strip_rows) b->tuned = false;
+    }
     if (!b->tuned && b->Ly_option <= 0) {
         lbm_status st = autotune(b);
         if (st != LBM_OK) return bfail(st, "batch autotune failed");

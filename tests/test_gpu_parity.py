@@ -77,6 +77,14 @@ def test_cavity_128_1000_steps_north_star_bound():
     assert du / c.U <= 1e-5, du / c.U
 
 
+@pytest.mark.parametrize("rows", [1, 3])
+def test_short_work_items(rows):
+    """Work items of one and of three rows (ragged last segment) give the same
+    steps as the oracle: periodic domain and walled cavity with a lid."""
+    compare(wl.random_periodic(150, 29, 0.6, 0.02, seed=4), 40, cells_per_item=rows)
+    compare(wl.random_cavity_state(130, 23, 0.5, Re=70.0, seed=8), 40, cells_per_item=rows)
+
+
 def test_small_and_degenerate_sizes():
     for nx, ny in ((3, 3), (5, 4), (129, 3), (3, 130), (127, 9)):
         c = wl.random_cavity_state(nx, ny, 0.6, Re=20.0, seed=nx * ny)
