@@ -23,32 +23,32 @@
 #include "lbm_internal.h"
 
 namespace lbm {
-cudaError_t launch_batch_f32(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_batch_f16(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_batch_bf16(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_batch_f64(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
-int batch_blocks_f32(int gi_mode);
-int batch_blocks_f16(int gi_mode);
-int batch_blocks_bf16(int gi_mode);
-int batch_blocks_f64(int gi_mode);
+cudaError_t launch_batch_f32(int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_batch_f16(int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_batch_bf16(int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_batch_f64(int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s);
+int batch_blocks_f32(int gi_mode, bool forced);
+int batch_blocks_f16(int gi_mode, bool forced);
+int batch_blocks_bf16(int gi_mode, bool forced);
+int batch_blocks_f64(int gi_mode, bool forced);
 
-cudaError_t launch_batch_step(int storage, int gi_mode, const BatchArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_batch_step(int storage, int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s)
 {
     switch (storage) {
-    case LBM_STORAGE_F16: return launch_batch_f16(gi_mode, a, grid, s);
-    case LBM_STORAGE_BF16: return launch_batch_bf16(gi_mode, a, grid, s);
-    case LBM_STORAGE_F64: return launch_batch_f64(gi_mode, a, grid, s);
-    default: return launch_batch_f32(gi_mode, a, grid, s);
+    case LBM_STORAGE_F16: return launch_batch_f16(gi_mode, forced, a, grid, s);
+    case LBM_STORAGE_BF16: return launch_batch_bf16(gi_mode, forced, a, grid, s);
+    case LBM_STORAGE_F64: return launch_batch_f64(gi_mode, forced, a, grid, s);
+    default: return launch_batch_f32(gi_mode, forced, a, grid, s);
     }
 }
 
-int batch_blocks_per_sm(int storage, int gi_mode)
+int batch_blocks_per_sm(int storage, int gi_mode, bool forced)
 {
     switch (storage) {
-    case LBM_STORAGE_F16: return batch_blocks_f16(gi_mode);
-    case LBM_STORAGE_BF16: return batch_blocks_bf16(gi_mode);
-    case LBM_STORAGE_F64: return batch_blocks_f64(gi_mode);
-    default: return batch_blocks_f32(gi_mode);
+    case LBM_STORAGE_F16: return batch_blocks_f16(gi_mode, forced);
+    case LBM_STORAGE_BF16: return batch_blocks_bf16(gi_mode, forced);
+    case LBM_STORAGE_F64: return batch_blocks_f64(gi_mode, forced);
+    default: return batch_blocks_f32(gi_mode, forced);
     }
 }
 }  // namespace lbm
@@ -67,6 +67,7 @@ struct Slot {
     uint8_t *solid = nullptr;
     size_t bytes = 0;
     StepParams p{};
+    bool forced = false;  // uniform body force: stepped by the forced kernel variant
     bool running = false;
     double tol = 0;
     long max_steps = 0;
@@ -116,6 +117,8 @@ struct lbm_batch {
     cudaStream_t stream = nullptr, io_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_K = 0;
+    int graph_variants = 0;                 // bit 0: unforced launch captured, bit 1: forced launch
+    int variants = 0;                       // the same bits for the current active set
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;      // queue, records, slot bookkeeping
     std::mutex run_mu;  // one tick at a time
@@ -251,6 +254,7 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     d.f[0] = s.f[0];
     d.f[1] = s.f[1];
     d.forced = r.fx != 0.0 || r.fy != 0.0;
+    s.forced = d.forced != 0;
     cudaError_t e = cudaMemcpyAsync(b->d_desc + si, &d, sizeof(DomainDesc), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = launch_init_eq(p, b->storage, nullptr, nullptr, nullptr, s.f[b->parity], b->stream);
@@ -307,24 +311,32 @@ void admit_pending(lbm_batch *b)
 // Upload the active list and the item prefix sums; returns the active count.
 int build_active(lbm_batch *b, double &cells)
 {
-    int n = 0, total = 0;
+    int n = 0, total = 0, split = 0;
     cells = 0;
+    b->variants = 0;
     {
         std::lock_guard<std::mutex> lk(b->mu);
-        for (int k = 0; k < b->max_slots; ++k) {
-            const Slot &s = b->slots[k];
-            if (!s.used || !s.running) continue;
-            b->h_active[n] = k;
-            b->h_prefix[n] = total;
-            b->h_step0[n] = (unsigned int)b->records[s.id].steps;
-            total += s.p.nitems;
-            cells += (double)s.nx * s.ny;
-            ++n;
+        // the unforced domains first, then the forced ones: each group is one
+        // launch of its own kernel variant over a contiguous item range
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int k = 0; k < b->max_slots; ++k) {
+                const Slot &s = b->slots[k];
+                if (!s.used || !s.running || (int)s.forced != pass) continue;
+                b->h_active[n] = k;
+                b->h_prefix[n] = total;
+                b->h_step0[n] = (unsigned int)b->records[s.id].steps;
+                total += s.p.nitems;
+                cells += (double)s.nx * s.ny;
+                b->variants |= 1 << pass;
+                ++n;
+            }
+            if (pass == 0) split = total;
         }
     }
     b->h_prefix[n] = total;
     b->h_state->n_active = n;
     b->h_state->total_items = total;
+    b->h_state->split_items = split;
     cudaMemcpyAsync(b->d_active, b->h_active, (size_t)(n > 0 ? n : 1) * sizeof(int), cudaMemcpyHostToDevice,
                     b->stream);
     cudaMemcpyAsync(b->d_prefix, b->h_prefix, (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream);
@@ -334,7 +346,7 @@ int build_active(lbm_batch *b, double &cells)
     return n;
 }
 
-BatchArgs batch_args(const lbm_batch *b, int parity, int k)
+BatchArgs batch_args(const lbm_batch *b, int parity, int k, bool forced)
 {
     BatchArgs a;
     a.domains = b->d_desc;
@@ -346,10 +358,22 @@ BatchArgs batch_args(const lbm_batch *b, int parity, int k)
     a.parity = parity;
     a.step0 = b->d_step0;
     a.k = k;
+    a.forced = forced;
     return a;
 }
 
-int batch_grid(const lbm_batch *b) { return b->num_sms * batch_blocks_per_sm(b->storage, b->gi_mode); }
+int batch_grid(const lbm_batch *b, bool forced)
+{
+    return b->num_sms * batch_blocks_per_sm(b->storage, b->gi_mode, forced);
+}
+
+// One step of all running domains: a launch per force variant present.
+void launch_batch_all(lbm_batch *b, int parity, int k, const int grid[2])
+{
+    for (int v = 0; v < 2; ++v)
+        if (b->variants >> v & 1)
+            launch_batch_step(b->storage, b->gi_mode, v == 1, batch_args(b, parity, k, v == 1), grid[v], b->stream);
+}
 
 // Set the rows per item of every running domain and re-upload their descriptors.
 void apply_Ly(lbm_batch *b, int Ly)
@@ -394,7 +418,7 @@ double active_strip_rows(lbm_batch *b)
 lbm_status autotune(lbm_batch *b)
 {
     const double rows = active_strip_rows(b);
-    const int resident = b->num_sms * batch_blocks_per_sm(b->storage, b->gi_mode) * WARPS;
+    const int resident = b->num_sms * batch_blocks_per_sm(b->storage, b->gi_mode, false) * WARPS;
     int h = (int)ceil(rows / (4.0 * resident));
     h = h < 1 ? 1 : (h > 24 ? 24 : h);
     int cand[3] = {h > 1 ? (h + 1) / 2 : 1, h, h < 24 ? 2 * h : 32};
@@ -403,7 +427,7 @@ lbm_status autotune(lbm_batch *b)
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LBM_ERR_CUDA;
     const int reps = 4;  // even: the parity is unchanged
-    const int grid = batch_grid(b);
+    const int grid[2] = {batch_grid(b, false), batch_grid(b, true)};
     int last = -1;
     for (int c : cand) {
         if (c == last) continue;
@@ -412,8 +436,7 @@ lbm_status autotune(lbm_batch *b)
         double cells;
         build_active(b, cells);
         cudaEventRecord(e0, b->stream);
-        for (int r = 0; r < reps; ++r)
-            launch_batch_step(b->storage, b->gi_mode, batch_args(b, (b->parity + r) & 1, r), grid, b->stream);
+        for (int r = 0; r < reps; ++r) launch_batch_all(b, (b->parity + r) & 1, r, grid);
         cudaEventRecord(e1, b->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             cudaEventDestroy(e0);
@@ -442,16 +465,16 @@ lbm_status autotune(lbm_batch *b)
 
 lbm_status ensure_graph(lbm_batch *b)
 {
-    if (b->graph && b->graph_K == b->check_every) return LBM_OK;
+    if (b->graph && b->graph_K == b->check_every && b->graph_variants == b->variants) return LBM_OK;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
     cudaGraph_t g = nullptr;
-    const int grid = batch_grid(b);  // occupancy query before the capture starts
+    // occupancy queries before the capture starts
+    const int grid[2] = {batch_grid(b, false), batch_grid(b, true)};
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
-    for (int k = 0; k < b->check_every; ++k)
-        launch_batch_step(b->storage, b->gi_mode, batch_args(b, (b->parity + k) & 1, k), grid, b->stream);
+    for (int k = 0; k < b->check_every; ++k) launch_batch_all(b, (b->parity + k) & 1, k, grid);
     if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess) return LBM_ERR_CUDA;
     const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
@@ -460,6 +483,7 @@ lbm_status ensure_graph(lbm_batch *b)
         return LBM_ERR_CUDA;
     }
     b->graph_K = b->check_every;
+    b->graph_variants = b->variants;
     return LBM_OK;
 }
 

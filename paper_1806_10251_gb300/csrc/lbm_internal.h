@@ -161,6 +161,7 @@ struct alignas(128) DomainDesc {
 struct BatchState {
     int n_active;     // active domains
     int total_items;  // prefix[n_active]
+    int split_items;  // items of the unforced domains, which come first in the active list
 };
 
 struct BatchArgs {
@@ -172,6 +173,7 @@ struct BatchArgs {
     int *error;
     int parity;                 // source buffer of this step (all domains step together)
     const unsigned int *step0;  // per active index: the domain's step count at the start of the tick
+    int forced;                 // this launch covers the forced domains (items split .. total) or the others
     int k;                      // launch index within the tick (domain step = step0 + k)
 };
 
@@ -182,8 +184,8 @@ cudaError_t launch_step_f32(const StepParams &p, const CUtensorMap &tin, const C
 cudaError_t launch_step_f16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
 cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
 cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
-cudaError_t launch_batch_step(int storage, int gi_mode, const BatchArgs &a, int grid, cudaStream_t s);
-int batch_blocks_per_sm(int storage, int gi_mode);
+cudaError_t launch_batch_step(int storage, int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s);
+int batch_blocks_per_sm(int storage, int gi_mode, bool forced);
 int blocks_per_sm_f32(int gi_mode, bool forced);
 int blocks_per_sm_f16(int gi_mode, bool forced);
 int blocks_per_sm_bf16(int gi_mode, bool forced);

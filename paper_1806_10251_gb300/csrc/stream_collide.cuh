@@ -578,12 +578,9 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m)
     asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(m) : "memory");
 }
 
-// One time step of every active domain of a batch.  Items run over the active
-// domains' (strip, segment) lists back to back; a warp finds its item's domain
-// by binary search in the prefix sums.  The forced or unforced collision is
-// chosen per domain, so a domain's arithmetic does not depend on which other
-// domains share the launch.
-template <typename ST, int MODE>
+// One time step of every active domain of a batch that has (FORCED) or has no
+// body force (see stream_collide_x2_batch_kernel).
+template <typename ST, int MODE, bool FORCED>
 __global__ void __launch_bounds__(THREADS, MinBlocks<ST>::value)
 stream_collide_batch_kernel(const __grid_constant__ BatchArgs a)
 {
@@ -591,10 +588,11 @@ stream_collide_batch_kernel(const __grid_constant__ BatchArgs a)
     WarpCtx w;
     warp_begin<ST>(w, smem);
     bool abort = false;
-    const int total = a.state->total_items;
+    const int first = FORCED ? a.state->split_items : 0;
+    const int end = FORCED ? a.state->total_items : a.state->split_items;
     const int n_active = a.state->n_active;
     int last_slot = -1;
-    for (int item = next_item(w, a.work); item < total; item = next_item(w, a.work)) {
+    for (int item = first + next_item(w, a.work); item < end; item = first + next_item(w, a.work)) {
         int lo = 0, hi = n_active;  // prefix[lo] <= item < prefix[hi]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -604,8 +602,6 @@ stream_collide_batch_kernel(const __grid_constant__ BatchArgs a)
         const int slot = __ldg(a.active + lo);
         const DomainDesc &D = a.domains[slot];
         if (slot != last_slot) {
-            // the descriptors were written by host copies into global memory:
-            // acquire them for the tensor-map proxy before the first TMA use
             tensormap_acquire(&D.tload[a.parity]);
             tensormap_acquire(&D.tstore[a.parity ^ 1]);
             last_slot = slot;
@@ -614,11 +610,8 @@ stream_collide_batch_kernel(const __grid_constant__ BatchArgs a)
         const StepParams &p = D.p;
         const ST *fin = static_cast<const ST *>(D.f[a.parity]);
         const uint32_t step = __ldg(a.step0 + lo) + (uint32_t)a.k;
-        const bool ok = D.forced ? run_item<ST, MODE, true>(w, p, &D.tload[a.parity], &D.tstore[a.parity ^ 1], fin,
-                                                             local % p.nstrips, local / p.nstrips, step)
-                                 : run_item<ST, MODE, false>(w, p, &D.tload[a.parity], &D.tstore[a.parity ^ 1], fin,
-                                                              local % p.nstrips, local / p.nstrips, step);
-        if (!ok) {
+        if (!run_item<ST, MODE, FORCED>(w, p, &D.tload[a.parity], &D.tstore[a.parity ^ 1], fin, local % p.nstrips,
+                                        local / p.nstrips, step)) {
             abort = true;
             break;
         }
@@ -626,27 +619,30 @@ stream_collide_batch_kernel(const __grid_constant__ BatchArgs a)
     warp_end<ST>(w, abort, a.error, a.work);
 }
 
-template <typename ST>
-cudaError_t launch_batch_t(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s)
+template <typename ST, int MODE>
+cudaError_t launch_batch_mode(bool forced, const BatchArgs &a, int grid, cudaStream_t s)
 {
     using T = Tile<ST>;
-    switch (gi_mode) {
-    case LBM_GI_UNCORRECTED:
-        stream_collide_batch_kernel<ST, LBM_GI_UNCORRECTED><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
-        break;
-    case LBM_GI_CUBIC_ONLY:
-        stream_collide_batch_kernel<ST, LBM_GI_CUBIC_ONLY><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
-        break;
-    default: stream_collide_batch_kernel<ST, LBM_GI_FULL><<<grid, THREADS, T::SMEM_BYTES, s>>>(a); break;
-    }
+    if (forced) stream_collide_batch_kernel<ST, MODE, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
+    else stream_collide_batch_kernel<ST, MODE, false><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename ST, int MODE>
+template <typename ST>
+cudaError_t launch_batch_t(int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s)
+{
+    switch (gi_mode) {
+    case LBM_GI_UNCORRECTED: return launch_batch_mode<ST, LBM_GI_UNCORRECTED>(forced, a, grid, s);
+    case LBM_GI_CUBIC_ONLY: return launch_batch_mode<ST, LBM_GI_CUBIC_ONLY>(forced, a, grid, s);
+    default: return launch_batch_mode<ST, LBM_GI_FULL>(forced, a, grid, s);
+    }
+}
+
+template <typename ST, int MODE, bool FORCED>
 int batch_blocks_variant()
 {
     using T = Tile<ST>;
-    auto fn = stream_collide_batch_kernel<ST, MODE>;
+    auto fn = stream_collide_batch_kernel<ST, MODE, FORCED>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM_BYTES) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -660,12 +656,17 @@ int batch_blocks_variant()
 }
 
 template <typename ST>
-int batch_blocks_t(int gi_mode)
+int batch_blocks_t(int gi_mode, bool forced)
 {
     switch (gi_mode) {
-    case LBM_GI_UNCORRECTED: return batch_blocks_variant<ST, LBM_GI_UNCORRECTED>();
-    case LBM_GI_CUBIC_ONLY: return batch_blocks_variant<ST, LBM_GI_CUBIC_ONLY>();
-    default: return batch_blocks_variant<ST, LBM_GI_FULL>();
+    case LBM_GI_UNCORRECTED:
+        return forced ? batch_blocks_variant<ST, LBM_GI_UNCORRECTED, true>()
+                      : batch_blocks_variant<ST, LBM_GI_UNCORRECTED, false>();
+    case LBM_GI_CUBIC_ONLY:
+        return forced ? batch_blocks_variant<ST, LBM_GI_CUBIC_ONLY, true>()
+                      : batch_blocks_variant<ST, LBM_GI_CUBIC_ONLY, false>();
+    default:
+        return forced ? batch_blocks_variant<ST, LBM_GI_FULL, true>() : batch_blocks_variant<ST, LBM_GI_FULL, false>();
     }
 }
 

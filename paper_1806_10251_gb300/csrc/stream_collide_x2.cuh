@@ -547,8 +547,12 @@ stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_cons
     warp_end_x2<ST>(w, abort, p.error, p.work);
 }
 
-// One time step of every active domain of a batch (see stream_collide_batch_kernel).
-template <typename ST, int MODE>
+// One time step of every active domain of a batch that has (FORCED) or has no
+// body force: the items of one launch run over those domains' (strip, segment)
+// lists back to back, and a warp finds its item's domain by binary search in
+// the prefix sums.  A domain's arithmetic does not depend on which other
+// domains share the launch.
+template <typename ST, int MODE, bool FORCED>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS_BATCH_X2)
 stream_collide_x2_batch_kernel(const __grid_constant__ BatchArgs a)
 {
@@ -556,10 +560,11 @@ stream_collide_x2_batch_kernel(const __grid_constant__ BatchArgs a)
     WarpCtx w;
     warp_begin_x2<ST>(w, smem);
     bool abort = false;
-    const int total = a.state->total_items;
+    const int first = FORCED ? a.state->split_items : 0;
+    const int end = FORCED ? a.state->total_items : a.state->split_items;
     const int n_active = a.state->n_active;
     int last_slot = -1;
-    for (int item = next_item(w, a.work); item < total; item = next_item(w, a.work)) {
+    for (int item = first + next_item(w, a.work); item < end; item = first + next_item(w, a.work)) {
         int lo = 0, hi = n_active;  // prefix[lo] <= item < prefix[hi]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -579,11 +584,8 @@ stream_collide_x2_batch_kernel(const __grid_constant__ BatchArgs a)
         const ST *fin = static_cast<const ST *>(D.f[a.parity]);
         ST *fout = static_cast<ST *>(const_cast<void *>(D.f[a.parity ^ 1]));
         const uint32_t step = __ldg(a.step0 + lo) + (uint32_t)a.k;
-        const bool ok = D.forced ? run_item_x2<ST, MODE, true>(w, p, &D.tload[a.parity], fin, fout,
-                                                                local % p.nstrips, local / p.nstrips, step)
-                                 : run_item_x2<ST, MODE, false>(w, p, &D.tload[a.parity], fin, fout,
-                                                                 local % p.nstrips, local / p.nstrips, step);
-        if (!ok) {
+        if (!run_item_x2<ST, MODE, FORCED>(w, p, &D.tload[a.parity], fin, fout, local % p.nstrips,
+                                           local / p.nstrips, step)) {
             abort = true;
             break;
         }
@@ -652,30 +654,40 @@ int blocks_per_sm_x2_t(int gi_mode, bool forced)
     }
 }
 
-template <typename ST>
-cudaError_t launch_batch_x2_t(int gi_mode, const BatchArgs &a, int grid, cudaStream_t s)
+template <typename ST, int MODE>
+cudaError_t launch_batch_x2_mode(bool forced, const BatchArgs &a, int grid, cudaStream_t s)
 {
     using T = Tile2<ST>;
-    switch (gi_mode) {
-    case LBM_GI_UNCORRECTED:
-        stream_collide_x2_batch_kernel<ST, LBM_GI_UNCORRECTED><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
-        break;
-    case LBM_GI_CUBIC_ONLY:
-        stream_collide_x2_batch_kernel<ST, LBM_GI_CUBIC_ONLY><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
-        break;
-    default: stream_collide_x2_batch_kernel<ST, LBM_GI_FULL><<<grid, THREADS, T::SMEM_BYTES, s>>>(a); break;
-    }
+    if (forced) stream_collide_x2_batch_kernel<ST, MODE, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
+    else stream_collide_x2_batch_kernel<ST, MODE, false><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename ST>
-int batch_blocks_x2_t(int gi_mode)
+cudaError_t launch_batch_x2_t(int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s)
+{
+    switch (gi_mode) {
+    case LBM_GI_UNCORRECTED: return launch_batch_x2_mode<ST, LBM_GI_UNCORRECTED>(forced, a, grid, s);
+    case LBM_GI_CUBIC_ONLY: return launch_batch_x2_mode<ST, LBM_GI_CUBIC_ONLY>(forced, a, grid, s);
+    default: return launch_batch_x2_mode<ST, LBM_GI_FULL>(forced, a, grid, s);
+    }
+}
+
+template <typename ST, int MODE>
+int batch_blocks_x2_mode(bool forced)
 {
     using T = Tile2<ST>;
+    return forced ? occupancy_of(stream_collide_x2_batch_kernel<ST, MODE, true>, T::SMEM_BYTES)
+                  : occupancy_of(stream_collide_x2_batch_kernel<ST, MODE, false>, T::SMEM_BYTES);
+}
+
+template <typename ST>
+int batch_blocks_x2_t(int gi_mode, bool forced)
+{
     switch (gi_mode) {
-    case LBM_GI_UNCORRECTED: return occupancy_of(stream_collide_x2_batch_kernel<ST, LBM_GI_UNCORRECTED>, T::SMEM_BYTES);
-    case LBM_GI_CUBIC_ONLY: return occupancy_of(stream_collide_x2_batch_kernel<ST, LBM_GI_CUBIC_ONLY>, T::SMEM_BYTES);
-    default: return occupancy_of(stream_collide_x2_batch_kernel<ST, LBM_GI_FULL>, T::SMEM_BYTES);
+    case LBM_GI_UNCORRECTED: return batch_blocks_x2_mode<ST, LBM_GI_UNCORRECTED>(forced);
+    case LBM_GI_CUBIC_ONLY: return batch_blocks_x2_mode<ST, LBM_GI_CUBIC_ONLY>(forced);
+    default: return batch_blocks_x2_mode<ST, LBM_GI_FULL>(forced);
     }
 }
 
