@@ -242,6 +242,7 @@ cudaError_t launch_fields(const StepParams &p, int storage, const void *f, doubl
 // the velocity snapshot is replaced.  Pass 2: one block reduces the rows in a
 // fixed order (deterministic).
 constexpr int RES_THREADS = 256;
+constexpr int RES_CELLS = 4;  // cells of a row per thread and iteration
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -271,25 +272,65 @@ __device__ __forceinline__ void block_sum5(double (&v)[5], double *out)
 }
 
 template <typename ST>
-__global__ void residual_pass1(const StepParams p, const ST *f, double half_ig, double *snap_ux, double *snap_uy,
-                               double *partials)
+__global__ void residual_pass1(const StepParams p, const ST *__restrict__ f, double half_ig,
+                               double *__restrict__ snap_ux, double *__restrict__ snap_uy, double *partials)
 {
+    // Per cell in the storage's compute precision R; each thread's sums over
+    // the cells it meets in one row (at most nx / blockDim.x of them) are kept
+    // in R and added into the FP64 accumulators row by row.  The density sum
+    // is formed as (fluid cells) + sum(rho - 1), the momentum directly as
+    // rho u = sum g e - F/(2 gamma).  A thread takes RES_CELLS cells of a row
+    // at a time and issues all their loads before any store (memory-level
+    // parallelism: the kernel is bound by DRAM latency otherwise).
+    using R = typename AuxReal<ST>::R;
+    const R hig = (R)half_ig, Fx0 = (R)p.Fx, Fy0 = (R)p.Fy;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int y = blockIdx.x; y < p.ny; y += gridDim.x) {
-        for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
-            if (solid_at(p, x, y)) continue;
-            const size_t c = (size_t)y * p.nx + x;
-            double r, u, v;
-            local_fields(p, f, x, y, half_ig, r, u, v);
-            const double du = u - snap_ux[c], dv = v - snap_uy[c];
-            acc[0] += du * du + dv * dv;
-            acc[1] += u * u + v * v;
-            acc[2] += r;
-            acc[3] += r * u;
-            acc[4] += r * v;
-            snap_ux[c] = u;
-            snap_uy[c] = v;
+        R du2 = 0, u2 = 0, sdr = 0, sjx = 0, sjy = 0;
+        int cnt = 0;
+        for (int x0 = threadIdx.x; x0 < p.nx; x0 += RES_CELLS * blockDim.x) {
+            R g[RES_CELLS][9], sx[RES_CELLS], sy[RES_CELLS], fx[RES_CELLS], fy[RES_CELLS];
+            bool ok[RES_CELLS];
+#pragma unroll
+            for (int j = 0; j < RES_CELLS; ++j) {
+                const int x = x0 + j * blockDim.x;
+                ok[j] = x < p.nx && !solid_at(p, x, y);
+                const size_t i = (size_t)y * p.pitch + (ok[j] ? x : 0);
+                const size_t c = (size_t)y * p.nx + (ok[j] ? x : 0);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) g[j][a] = ldr(f, (size_t)a * p.plane + i);
+                sx[j] = (R)snap_ux[c];
+                sy[j] = (R)snap_uy[c];
+                fx[j] = p.force ? (R)p.force[i] : Fx0;
+                fy[j] = p.force ? (R)p.force[(size_t)p.plane + i] : Fy0;
+            }
+#pragma unroll
+            for (int j = 0; j < RES_CELLS; ++j) {
+                if (!ok[j]) continue;
+                const R *q = g[j];
+                const R dr = q[0] + (q[1] + q[3]) + (q[2] + q[4]) + ((q[5] + q[6]) + (q[7] + q[8]));
+                const R jx = (q[1] - q[3]) + (q[5] - q[6]) + (q[8] - q[7]);
+                const R jy = (q[2] - q[4]) + (q[5] + q[6]) - (q[7] + q[8]);
+                const R mx = jx - fx[j] * hig, my = jy - fy[j] * hig;
+                const R ir = recip_aux(R(1) + dr);
+                const R u = mx * ir, v = my * ir;
+                const R du = u - sx[j], dv = v - sy[j];
+                du2 += du * du + dv * dv;
+                u2 += u * u + v * v;
+                sdr += dr;
+                sjx += mx;
+                sjy += my;
+                ++cnt;
+                const size_t c = (size_t)y * p.nx + x0 + j * blockDim.x;
+                snap_ux[c] = (double)u;
+                snap_uy[c] = (double)v;
+            }
         }
+        acc[0] += (double)du2;
+        acc[1] += (double)u2;
+        acc[2] += (double)cnt + (double)sdr;
+        acc[3] += (double)sjx;
+        acc[4] += (double)sjy;
     }
     block_sum5<RES_THREADS>(acc, partials + (size_t)blockIdx.x * 5);
 }
