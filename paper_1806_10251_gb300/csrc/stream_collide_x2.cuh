@@ -57,7 +57,7 @@ template <> struct PairIO<float> {
     {
         *reinterpret_cast<float2 *>(p) = make_float2(v.x, v.y);
     }
-    __device__ static __forceinline__ void stg2_sr(float *p, F2 v, uint32_t, uint32_t) { stg2(p, v); }
+    __device__ static __forceinline__ void stg2_sr(float *p, F2 v, uint32_t) { stg2(p, v); }
 };
 template <> struct PairIO<__half> {  // holds F16_SCALE * g
     __device__ static __forceinline__ F2 from_h2(__half2 h)
@@ -72,12 +72,16 @@ template <> struct PairIO<__half> {  // holds F16_SCALE * g
         const F2 s = v * f2(F16_SCALE);
         *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(s.x, s.y);
     }
-    __device__ static __forceinline__ void stg2_sr(__half *p, F2 v, uint32_t r0, uint32_t r1)
+    // r: 32 random bits; the even cell takes bits 19..31, the odd cell bits
+    // 6..18 (13 dropped bits each for a normal FP16 result); one truncating
+    // conversion packs both
+    __device__ static __forceinline__ void stg2_sr(__half *p, F2 v, uint32_t r)
     {
-        const F2 s = v * f2(F16_SCALE);  // 13 dropped bits for a normal FP16 result
-        const __half lo = __float2half_rz(__uint_as_float(__float_as_uint(s.x) + (r0 >> 19)));
-        const __half hi = __float2half_rz(__uint_as_float(__float_as_uint(s.y) + (r1 >> 19)));
-        *reinterpret_cast<__half2 *>(p) = __halves2half2(lo, hi);
+        const F2 s = v * f2(F16_SCALE);
+        const uint32_t lo = __float_as_uint(s.x) + (r >> 19), hi = __float_as_uint(s.y) + ((r >> 6) & 0x1fffu);
+        uint32_t d;
+        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
+        *reinterpret_cast<uint32_t *>(p) = d;
     }
 };
 template <> struct PairIO<__nv_bfloat16> {
@@ -98,11 +102,14 @@ template <> struct PairIO<__nv_bfloat16> {
     {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
     }
-    __device__ static __forceinline__ void stg2_sr(__nv_bfloat16 *p, F2 v, uint32_t r0, uint32_t r1)
+    // r: 32 random bits; the even cell takes the upper 16, the odd cell the
+    // lower 16 (16 dropped bits each); one truncating conversion packs both
+    __device__ static __forceinline__ void stg2_sr(__nv_bfloat16 *p, F2 v, uint32_t r)
     {
-        const __nv_bfloat16 lo = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v.x) + (r0 >> 16)));
-        const __nv_bfloat16 hi = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v.y) + (r1 >> 16)));
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(lo, hi);
+        const uint32_t lo = __float_as_uint(v.x) + (r >> 16), hi = __float_as_uint(v.y) + (r & 0xffffu);
+        uint32_t d;
+        asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
+        *reinterpret_cast<uint32_t *>(p) = d;
     }
 };
 
@@ -496,9 +503,9 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         ST *fo = fout + (size_t)y * p.pitch + xe;
         if (sround) {
             const uint32_t cell = (uint32_t)(y * p.nx + xe);
-            const uint32_t h0 = mix32(seed ^ cell), h1 = mix32(seed ^ (cell + 1u));
+            const uint32_t h = mix32(seed ^ cell);  // one hash per pair of cells
 #pragma unroll
-            for (int a = 0; a < 9; ++a) IO::stg2_sr(fo + a * plane, out[a], sr_bits(h0, a), sr_bits(h1, a));
+            for (int a = 0; a < 9; ++a) IO::stg2_sr(fo + a * plane, out[a], sr_bits(h, a));
         } else {
 #pragma unroll
             for (int a = 0; a < 9; ++a) IO::stg2(fo + a * plane, out[a]);
