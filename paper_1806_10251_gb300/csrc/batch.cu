@@ -411,7 +411,7 @@ double active_strip_rows(lbm_batch *b)
 // works through its item's rows one after another, so the item height bounds
 // the latency of a launch when there is little work, while short items re-read
 // more halo rows when there is much.  The starting point gives about four
-// items per resident warp over the whole active set (1..24 rows); the
+// items per resident warp over the whole active set (1..16 rows); the
 // candidates h/2, h, 2h are then timed on a few steps of the current batch
 // (the steps count) and the fastest kept.  Chosen again whenever the active
 // work has changed by more than a factor of two.
@@ -420,8 +420,8 @@ lbm_status autotune(lbm_batch *b)
     const double rows = active_strip_rows(b);
     const int resident = b->num_sms * batch_blocks_per_sm(b->storage, b->gi_mode, false) * WARPS;
     int h = (int)ceil(rows / (4.0 * resident));
-    h = h < 1 ? 1 : (h > 24 ? 24 : h);
-    int cand[3] = {h > 1 ? (h + 1) / 2 : 1, h, h < 24 ? 2 * h : 32};
+    h = h < 1 ? 1 : (h > 16 ? 16 : h);
+    int cand[3] = {h > 1 ? (h + 1) / 2 : 1, h, h < 16 ? 2 * h : 24};
     float best_ms = 1e30f;
     int best = h;
     cudaEvent_t e0, e1;
