@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--e2e-check-every", type=int, default=100)
     ap.add_argument("--cells-per-item", type=int, default=0,
                     help="rows per work item of the step kernel (0 = automatic)")
-    ap.add_argument("--workload", choices=["cavity", "batch", "serve"], default="cavity",
+    ap.add_argument("--workload", choices=["cavity", "batch", "serve", "precision"], default="cavity",
                     help="cavity: the timed step of one large domain (default); batch: steady solves/s of "
                          "independent cavities, FP16 batch against the plain FP32 solver one domain at a time; "
                          "serve: a Poisson stream of steady-solve requests into the batch engine")
@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
     ap.add_argument("--side-min", type=int, default=128)
     ap.add_argument("--side-max", type=int, default=512)
+    ap.add_argument("--scale", type=int, default=16,
+                    help="precision: linear scale-down of the 8192 x 2048 obstacle channel")
     return ap.parse_args()
 
 
@@ -367,6 +369,58 @@ def run_serve(args, rank):
     return 0
 
 
+def run_precision(args, rank):
+    """Storage precision on a geometry-scaled copy of the obstacle channel
+    (8192 x 2048, square obstacle of side 128 centred at (1024, 1024), walls in
+    y, periodic in x, body force F_x = 8 nu U0 / H^2, Re = 40 on the obstacle,
+    U0 = 0.05, gamma = 0.3), every length divided by --scale.  Each storage
+    runs to its steady criterion (checks 10 000 steps apart); errors are relative
+    L2 against the FP64-storage run (the GPU FP64 path matches the oracle to
+    1e-12 per step): u over fluid cells, rho as sum (rho - rho64)^2 over
+    sum (rho64 - mean rho64)^2."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1806_10251_gb300 import lbm
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    k = args.scale
+    c = wl.channel_obstacle(nx=8192 // k, ny=2048 // k, D=128 // k, Re=40.0, U0=0.05, gamma=0.3, xc=1024 // k)
+    fluid = c.solid == 0
+    runs = [("f64", 3, 1, 1e-10), ("f32", 0, 1, 2e-7), ("f16", 1, 1, 1e-3), ("bf16", 2, 1, 1e-2),
+            ("f16_nearest", 1, 0, 1e-3)]
+    out, ref = [], None
+    for name, st, sr, tol in runs:
+        g = lbm.solver_from_case(c, storage=st)
+        if st in (1, 2):
+            g.set_option("stochastic_rounding", sr)
+        t0 = time.perf_counter()
+        status, steps, r = g.run_to_steady(tol, args.check_every, args.max_steps, raise_on_error=False)
+        dt = time.perf_counter() - t0
+        rho, ux, uy = g.fields()
+        g.close()
+        if ref is None:
+            ref = (rho, ux, uy)
+        r64, u64, v64 = ref
+        l2u = rel_l2(ux, uy, u64, v64, fluid)
+        d = rho - r64
+        l2r = float(np.sqrt((d[fluid] ** 2).sum() / ((r64[fluid] - r64[fluid].mean()) ** 2).sum()))
+        du = float(max(np.abs(ux - u64)[fluid].max(), np.abs(uy - v64)[fluid].max()) / c.U)
+        out.append({"storage": name, "status": int(status), "steps": int(steps), "residual": float(r), "tol": tol,
+                    "seconds": dt, "l2_u": l2u, "l2_rho": l2r, "max_du_over_U0": du,
+                    "u_max": float(np.abs(ux[fluid]).max())})
+    line = {"metric": "steady-state error of u and rho per storage format against FP64 storage",
+            "workload": "precision", "value": out[2]["l2_u"], "unit": "relative L2 of u (FP16)",
+            "higher_is_better": False, "runs": out,
+            "config": {"case": c.name, "scale": k, "nx": c.nx, "ny": c.ny, "nu": c.nu, "Fx": c.Fx,
+                       "gamma": c.gamma, "check_every": args.check_every, "max_steps": args.max_steps},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -376,6 +430,8 @@ def main():
         return run_batch(args, rank)
     if args.workload == "serve":
         return run_serve(args, rank)
+    if args.workload == "precision":
+        return run_precision(args, rank)
 
     import numpy as np
     import torch
