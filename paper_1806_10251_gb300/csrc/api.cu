@@ -165,7 +165,19 @@ StepParams make_params(const lbm_ctx *c)
     if (Ly > c->ny) Ly = c->ny;
     p.Ly = Ly;
     const int nseg = (c->ny + Ly - 1) / Ly;
+    p.nseg = nseg;
+    p.nwave = 1;
+    p.nseg_phase = nseg;
     p.nitems = p.nstrips * nseg;
+    if (c->storage != LBM_STORAGE_F64) {
+        // one phase of segments per wave of resident warps (see StepParams)
+        const int waves = (int)((double)p.nitems / resident + 0.5);
+        if (waves > 1 && waves < nseg) {
+            p.nwave = waves;
+            p.nseg_phase = (nseg + waves - 1) / waves;
+            p.nitems = p.nstrips * p.nseg_phase * waves;
+        }
+    }
     return p;
 }
 

@@ -163,7 +163,10 @@ void set_geometry(StepParams &p, int Ly, int storage)
 {
     p.nstrips = (p.nx + strip_width(storage) - 1) / strip_width(storage);
     p.Ly = Ly < p.ny ? Ly : p.ny;
-    p.nitems = p.nstrips * ((p.ny + p.Ly - 1) / p.Ly);
+    p.nseg = (p.ny + p.Ly - 1) / p.Ly;
+    p.nwave = 1;  // segment-major order inside a batch
+    p.nseg_phase = p.nseg;
+    p.nitems = p.nstrips * p.nseg;
 }
 
 // Allocate and initialise one admitted request (rest state, lid or walls).

@@ -138,6 +138,11 @@ struct StepParams {
     unsigned int *work;      // device work counters {next item, warps done}, zero between launches
     // work decomposition: items = warp strips x segments, each segment Ly rows
     int Ly, nstrips, nitems;
+    // item order of the single-domain kernel: segments are handed out in nwave
+    // phases (phase q: segments q, q + nwave, ...; nseg_phase of them per strip)
+    // so that a segment starts when the one above it ends and re-reads their
+    // shared boundary rows while they are still in L2; nwave = 1: segment-major
+    int nseg, nwave, nseg_phase;
     // 16-bit storage: round the stored deviations stochastically (nonzero) or
     // to nearest; the random bits are a hash of (step, cell, direction)
     int sround;

@@ -546,7 +546,13 @@ stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_cons
     warp_begin_x2<ST>(w, smem);
     bool abort = false;
     for (int item = next_item(w, p.work); item < p.nitems; item = next_item(w, p.work)) {
-        if (!run_item_x2<ST, MODE, FORCED>(w, p, &tin, fin, fout, item % p.nstrips, item / p.nstrips, p.step)) {
+        // phase-ordered items (see StepParams::nwave); items past the last
+        // segment of a phase are empty
+        const int per = p.nstrips * p.nseg_phase;
+        const int phase = item / per, r = item - phase * per;
+        const int strip = r % p.nstrips, seg = phase + (r / p.nstrips) * p.nwave;
+        if (seg >= p.nseg) continue;
+        if (!run_item_x2<ST, MODE, FORCED>(w, p, &tin, fin, fout, strip, seg, p.step)) {
             abort = true;
             break;
         }
