@@ -62,8 +62,10 @@ def parse():
     ap.add_argument("--max-steps", type=int, default=400000)
     ap.add_argument("--accuracy-sample", type=int, default=6,
                     help="batch: smallest domains whose results are compared with a converged FP32 solve")
-    ap.add_argument("--requests", type=int, default=60)
-    ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=2.0, help="serve: mean arrivals per second")
+    ap.add_argument("--request-max-steps", type=int, default=100000,
+                    help="serve: steps after which a request is returned as not converged")
     ap.add_argument("--side-min", type=int, default=128)
     ap.add_argument("--side-max", type=int, default=512)
     ap.add_argument("--scale", type=int, default=16,
@@ -333,7 +335,7 @@ def run_serve(args, rank):
                     pending.discard(rid)
                     b.release(rid)
             time.sleep(min(0.002, ta - now))
-        rid = b.submit_case(c, tol=args.tol, max_steps=args.max_steps)
+        rid = b.submit_case(c, tol=args.tol, max_steps=args.request_max_steps)
         ids.append(rid)
         pending.add(rid)
         st = b.stats()
@@ -362,6 +364,7 @@ def run_serve(args, rank):
             "max_running": int(max(d[0] for d in depth)), "max_queued": int(max(d[1] for d in depth)),
             "converged": int(sum(done[i].state == lbm.REQ_CONVERGED for i in ids)), "requests": len(ids),
             "config": {"rate_per_s": args.rate, "requests": args.requests, "side": [args.side_min, args.side_max],
+                       "request_max_steps": args.request_max_steps,
                        "tol": args.tol, "check_every": args.check_every, "budget_bytes": budget,
                        "stream": "poisson_requests(seed=0)"},
             "data": "synthetic"}
