@@ -417,31 +417,20 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         for (int k = 0; k < min(T::NSLOT, nsrc); ++k) issue(k);
         issued = min(T::NSLOT, nsrc);
     }
-    const bool ok = land(0) && land(1) && land(2) && land(3);
-    if (!ok) return false;
+    if (!(land(0) && land(1))) return false;
     // cur = populations of row y, nxt = row y + 1; densities of rows y-1, y, y+1
+    // (filled by the two warm-up passes of the row loop, y = y0-2 and y0-1)
     F2 cur[9], nxt[9];
-    int cur_valid, nxt_valid;
-    F2 rm, r0, rp;
-    R hl0, hr0, hlp, hrp, d0, d1;
-    auto produce_any = [&](int r, F2(&g)[9], int &valid, F2 &rho, R &rho_l, R &rho_r) {
-        if (strip_fast && (p.pery || (r >= 1 && r <= p.ny - 2)))
-            produce(Flag<true>(), r, g, valid, rho, rho_l, rho_r);
-        else
-            produce(Flag<false>(), r, g, valid, rho, rho_l, rho_r);
-    };
-    produce_any(y0 - 1, nxt, nxt_valid, rm, d0, d1);
-    produce_any(y0, cur, cur_valid, r0, hl0, hr0);
-    __syncwarp();
-    if (lane == 0) {
-        // source row y0 - 2 is no longer read: refill its slot
-        const int kmax = min(nsrc - 1, T::NSLOT);
-        if (issued <= kmax) fence_proxy_async();
-        while (issued <= kmax) issue(issued++);
-    }
+    int cur_valid = 0, nxt_valid = 0;
+    F2 rm = f2(-1.f), r0 = f2(-1.f), rp;
+    R hl0 = R(-1), hr0 = R(-1), hlp, hrp;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) cur[a] = f2(0.f);
     const size_t plane = (size_t)p.plane;
 
-    // One time-step row: land source y + 2, produce row y + 1, collide row y.
+    // One pass: land source y + 2, produce row y + 1, collide row y (rows
+    // y >= y0; the passes y0-2 and y0-1 only produce, so the item needs no
+    // separate prologue code).
     auto iter = [&](auto fast_tag, int y) -> bool {
         constexpr bool FAST = decltype(fast_tag)::value;
         const int kl = y - y0 + 4;  // source row y + 2
@@ -453,6 +442,16 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
             const int kmax = min(nsrc - 1, y - y0 + 2 + T::NSLOT);
             if (issued <= kmax) fence_proxy_async();
             while (issued <= kmax) issue(issued++);
+        }
+        if (y < y0) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) cur[a] = nxt[a];
+            cur_valid = nxt_valid;
+            rm = r0;
+            r0 = rp;
+            hl0 = hlp;
+            hr0 = hrp;
+            return true;
         }
         // density gradient by central differences: x neighbours of the pair by
         // shuffles (odd cell of the lane to the left, even cell of the one to
@@ -519,15 +518,15 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         hr0 = hrp;
         return true;
     };
-    // rows whose iteration is boundary-free: y and y + 1 both fast rows
+    // passes without boundary logic: rows y and y + 1 both fast rows
     int yf0 = y1, yf1 = y1;
     if (strip_fast) {
-        yf0 = p.pery ? y0 : max(y0, 1);
+        yf0 = p.pery ? y0 - 2 : max(y0 - 2, 1);
         yf1 = p.pery ? y1 : min(y1, p.ny - 2);
         if (yf1 < yf0) yf0 = yf1 = y1;
     }
     bool abort = false;
-    for (int y = y0; y < yf0 && !abort; ++y) abort = !iter(Flag<false>(), y);
+    for (int y = y0 - 2; y < yf0 && !abort; ++y) abort = !iter(Flag<false>(), y);
     for (int y = yf0; y < yf1 && !abort; ++y) abort = !iter(Flag<true>(), y);
     for (int y = max(yf1, yf0); y < y1 && !abort; ++y) abort = !iter(Flag<false>(), y);
     if (abort) return false;
