@@ -97,7 +97,8 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U,
  *   "stochastic_rounding" FP16/BF16 storage: 1 (default) rounds each stored
  *               deviation up or down with probability given by its distance
  *               to the two neighbours (random bits: a hash of step, cell and
- *               direction, so runs are reproducible); 0 rounds to nearest */
+ *               direction, so runs are reproducible); 0 rounds to nearest
+ *               (ties away from zero) */
 lbm_status lbm_set_option(lbm_ctx *ctx, const char *key, double value);
 lbm_status lbm_get_option(lbm_ctx *ctx, const char *key, double *value);
 

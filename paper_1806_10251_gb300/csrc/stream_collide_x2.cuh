@@ -58,6 +58,7 @@ template <> struct PairIO<float> {
         *reinterpret_cast<float2 *>(p) = make_float2(v.x, v.y);
     }
     __device__ static __forceinline__ void stg2_sr(float *p, F2 v, uint32_t) { stg2(p, v); }
+    static constexpr uint32_t HALF_ULP = 0u;
 };
 template <> struct PairIO<__half> {  // holds F16_SCALE * g
     __device__ static __forceinline__ F2 from_h2(__half2 h)
@@ -74,7 +75,9 @@ template <> struct PairIO<__half> {  // holds F16_SCALE * g
     }
     // r: 32 random bits; the even cell takes bits 19..31, the odd cell bits
     // 6..18 (13 dropped bits each for a normal FP16 result); one truncating
-    // conversion packs both
+    // conversion packs both.  HALF_ULP in place of random bits adds half of the
+    // dropped range: rounding to nearest, ties away from zero.
+    static constexpr uint32_t HALF_ULP = 0x80040000u;
     __device__ static __forceinline__ void stg2_sr(__half *p, F2 v, uint32_t r)
     {
         const F2 s = v * f2(F16_SCALE);
@@ -103,7 +106,9 @@ template <> struct PairIO<__nv_bfloat16> {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
     }
     // r: 32 random bits; the even cell takes the upper 16, the odd cell the
-    // lower 16 (16 dropped bits each); one truncating conversion packs both
+    // lower 16 (16 dropped bits each); one truncating conversion packs both.
+    // HALF_ULP: rounding to nearest, ties away from zero.
+    static constexpr uint32_t HALF_ULP = 0x80008000u;
     __device__ static __forceinline__ void stg2_sr(__nv_bfloat16 *p, F2 v, uint32_t r)
     {
         const uint32_t lo = __float_as_uint(v.x) + (r >> 16), hi = __float_as_uint(v.y) + (r & 0xffffu);
@@ -500,11 +505,12 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         // 2-wide stores of the row (x0 + SW <= pitch: the odd cell past nx, if
         // any, lands in the row padding)
         ST *fo = fout + (size_t)y * p.pitch + xe;
-        if (sround) {
-            const uint32_t cell = (uint32_t)(y * p.nx + xe);
-            const uint32_t h = mix32(seed ^ cell);  // one hash per pair of cells
+        if constexpr (StorageTraits<ST>::kReduced) {
+            // one store path for both rounding modes (no cold alternative in the loop)
+            const uint32_t h = mix32(seed ^ (uint32_t)(y * p.nx + xe));  // one hash per pair of cells
 #pragma unroll
-            for (int a = 0; a < 9; ++a) IO::stg2_sr(fo + a * plane, out[a], sr_bits(h, a));
+            for (int a = 0; a < 9; ++a)
+                IO::stg2_sr(fo + a * plane, out[a], sround ? sr_bits(h, a) : IO::HALF_ULP);
         } else {
 #pragma unroll
             for (int a = 0; a < 9; ++a) IO::stg2(fo + a * plane, out[a]);
