@@ -16,7 +16,7 @@ namespace lbm {
 
 __device__ __forceinline__ F2 ld(const float2 &v) { return F2{v.x, v.y}; }
 
-template <int MODE, bool FORCED>
+template <int MODE, bool FORCED, bool GUARD = false>
 __device__ __forceinline__ void collide_x2(F2 (&g)[9], F2 drx, F2 dry, F2 Fx, F2 Fy, const Consts2 &k,
                                            bool guard, unsigned long long *guard_count)
 {
@@ -85,7 +85,7 @@ __device__ __forceinline__ void collide_x2(F2 (&g)[9], F2 drx, F2 dry, F2 Fx, F2
         F2 c1 = (ld(k.a3) + P) * rho, c2 = (ld(k.a3) + Q) * rho;
         F2 c1t = (ld(k.a4) + Pt) * rho, c2t = (ld(k.a4) + Qt) * rho;
         F2 D = neg2(fma2(c1, c2t, c1t * c2));
-        if (guard) {
+        if (GUARD && guard) {
             // per cell: drop the velocity-dependent parts where |D| < 0.1 |D0|
             const F2 a3r = ld(k.a3) * rho, a4r = ld(k.a4) * rho;
             const F2 D0 = ld(k.m_two) * (a3r * a4r);

@@ -174,7 +174,7 @@ __device__ __forceinline__ void warp_end_x2(WarpCtx &w, bool abort, int *error, 
 // One work item: rows [seg*Ly, ...) of the 64-column strip `strip` of the
 // domain described by p, reading fin through tin (wide load box) and writing
 // fout directly.  Returns false when a bounded wait expired.
-template <typename ST, int MODE, bool FORCED>
+template <typename ST, int MODE, bool FORCED, bool GUARD = false>
 __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, const CUtensorMap *tin,
                                             const ST *__restrict__ fin, ST *__restrict__ fout, int strip, int seg,
                                             uint32_t step)
@@ -223,13 +223,16 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
             tma_load_3d(ring_u32 + slot * T::SLOT_BYTES, tin, x0 - T::PAD, s, 0, bar);
         }
     };
-    // all lanes: wait for item row k, patch periodic x halo columns
-    auto land = [&](int k) -> bool {
+    // all lanes: wait for item row k, patch periodic x halo columns (FIX: the
+    // item is an end strip of a periodic domain; a compile-time flag keeps the
+    // patch code out of the other items' row loop)
+    auto land = [&](auto fix_tag, int k) -> bool {
+        constexpr bool FIX = decltype(fix_tag)::value;
         const int slot = slot_of(k);
         const uint32_t parity = ((q_base + (uint32_t)k) / T::NSLOT) & 1u;
         const bool ok = mbar_wait_bounded(bars_u32 + 8 * slot, parity);
         if (__any_sync(FULL, !ok)) return false;
-        if (fix_left || fix_right) {
+        if (FIX) {
             int s = s_first + k;
             if (p.pery) s = wrap(s, p.ny);
             if (s >= 0 && s < p.ny) {
@@ -422,7 +425,9 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         for (int k = 0; k < min(T::NSLOT, nsrc); ++k) issue(k);
         issued = min(T::NSLOT, nsrc);
     }
-    if (!(land(0) && land(1))) return false;
+    const bool fix = fix_left || fix_right;
+    if (fix ? !(land(Flag<true>(), 0) && land(Flag<true>(), 1)) : !(land(Flag<false>(), 0) && land(Flag<false>(), 1)))
+        return false;
     // cur = populations of row y, nxt = row y + 1; densities of rows y-1, y, y+1
     // (filled by the two warm-up passes of the row loop, y = y0-2 and y0-1)
     F2 cur[9], nxt[9];
@@ -436,10 +441,10 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
     // One pass: land source y + 2, produce row y + 1, collide row y (rows
     // y >= y0; the passes y0-2 and y0-1 only produce, so the item needs no
     // separate prologue code).
-    auto iter = [&](auto fast_tag, int y) -> bool {
+    auto iter = [&](auto fast_tag, auto fix_tag, int y) -> bool {
         constexpr bool FAST = decltype(fast_tag)::value;
         const int kl = y - y0 + 4;  // source row y + 2
-        if (kl < nsrc && !land(kl)) return false;
+        if (kl < nsrc && !land(fix_tag, kl)) return false;
         produce(fast_tag, y + 1, nxt, nxt_valid, rp, hlp, hrp);
         __syncwarp();
         if (lane == 0) {
@@ -493,7 +498,8 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
 #pragma unroll
         for (int a = 0; a < 9; ++a) out[a] = cur[a];
         const F2 half = ld(p.c2.half);
-        collide_x2<MODE, FORCED>(out, half * (re - rw), half * (rn - rs), Fx, Fy, p.c2, p.guard != 0, p.guard_count);
+        collide_x2<MODE, FORCED, GUARD>(out, half * (re - rw), half * (rn - rs), Fx, Fy, p.c2, p.guard != 0,
+                                        p.guard_count);
         if (!FAST && cur_valid != 3) {
 #pragma unroll
             for (int k = 0; k < 2; ++k)
@@ -532,16 +538,21 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         if (yf1 < yf0) yf0 = yf1 = y1;
     }
     bool abort = false;
-    for (int y = y0 - 2; y < yf0 && !abort; ++y) abort = !iter(Flag<false>(), y);
-    for (int y = yf0; y < yf1 && !abort; ++y) abort = !iter(Flag<true>(), y);
-    for (int y = max(yf1, yf0); y < y1 && !abort; ++y) abort = !iter(Flag<false>(), y);
+    auto rows = [&](auto fix_tag) {
+        for (int y = y0 - 2; y < yf0 && !abort; ++y) abort = !iter(Flag<false>(), fix_tag, y);
+        for (int y = yf0; y < yf1 && !abort; ++y) abort = !iter(Flag<true>(), fix_tag, y);
+        for (int y = max(yf1, yf0); y < y1 && !abort; ++y) abort = !iter(Flag<false>(), fix_tag, y);
+    };
+    if (fix) rows(Flag<true>());
+    else rows(Flag<false>());
     if (abort) return false;
     w.q_base += (uint32_t)nsrc;
     return true;
 }
 
-// One time step of one domain.
-template <typename ST, int MODE, bool FORCED>
+// One time step of one domain (GUARD: the variant with the strain-solve guard,
+// launched only when a context turns the guard on).
+template <typename ST, int MODE, bool FORCED, bool GUARD = false>
 __global__ void __launch_bounds__(THREADS, FORCED ? MIN_BLOCKS_BATCH_X2 : MIN_BLOCKS_X2)
 stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_constant__ CUtensorMap tin,
                          const ST *__restrict__ fin, ST *__restrict__ fout)
@@ -557,7 +568,7 @@ stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_cons
         const int phase = item / per, r = item - phase * per;
         const int strip = r % p.nstrips, seg = phase + (r / p.nstrips) * p.nwave;
         if (seg >= p.nseg) continue;
-        if (!run_item_x2<ST, MODE, FORCED>(w, p, &tin, fin, fout, strip, seg, p.step)) {
+        if (!run_item_x2<ST, MODE, FORCED, GUARD>(w, p, &tin, fin, fout, strip, seg, p.step)) {
             abort = true;
             break;
         }
@@ -620,6 +631,12 @@ cudaError_t launch_step_x2_t(const StepParams &p, const CUtensorMap &tin, const 
     ST *out = static_cast<ST *>(fout);
     const bool forced = p.force != nullptr || p.Fx != 0.0 || p.Fy != 0.0;
 #define LBM_LAUNCH(M, F) stream_collide_x2_kernel<ST, M, F><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out)
+    if (p.guard && p.gi_mode == LBM_GI_FULL) {
+        // the guard acts in the full kernel only (the strain solve)
+        if (forced) stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
+        else stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
+        return cudaGetLastError();
+    }
     switch (p.gi_mode) {
     case LBM_GI_UNCORRECTED:
         if (forced) LBM_LAUNCH(LBM_GI_UNCORRECTED, true);
@@ -666,9 +683,14 @@ int blocks_per_sm_x2_t(int gi_mode, bool forced)
     case LBM_GI_CUBIC_ONLY:
         return forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, true>, T::SMEM_BYTES)
                       : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, false>, T::SMEM_BYTES);
-    default:
-        return forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true>, T::SMEM_BYTES)
-                      : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false>, T::SMEM_BYTES);
+    default: {
+        // the guard variants get their shared-memory attribute too (min of both)
+        const int a = forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true>, T::SMEM_BYTES)
+                             : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false>, T::SMEM_BYTES);
+        const int b = forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true>, T::SMEM_BYTES)
+                             : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true>, T::SMEM_BYTES);
+        return a < b ? a : b;
+    }
     }
 }
 
