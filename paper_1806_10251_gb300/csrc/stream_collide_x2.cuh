@@ -453,73 +453,65 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
             if (issued <= kmax) fence_proxy_async();
             while (issued <= kmax) issue(issued++);
         }
-        if (y < y0) {
+        if (y >= y0) {  // the warm-up passes only produce
+            // density gradient by central differences: x neighbours of the pair by
+            // shuffles (odd cell of the lane to the left, even cell of the one to
+            // the right), halo densities at the strip ends
+            R wl = __shfl_up_sync(FULL, r0.y, 1), er = __shfl_down_sync(FULL, r0.x, 1);
+            if (lane == 0) wl = hl0;
+            if (lane == 31) er = hr0;
+            F2 re = f2(r0.y, er), rw = f2(wl, r0.x);
+            F2 rn = rp, rs = rm;
+            if (!FAST) {
+                // a missing neighbour (wall side, solid) takes the cell's own density
 #pragma unroll
-            for (int a = 0; a < 9; ++a) cur[a] = nxt[a];
-            cur_valid = nxt_valid;
-            rm = r0;
-            r0 = rp;
-            hl0 = hlp;
-            hr0 = hrp;
-            return true;
-        }
-        // density gradient by central differences: x neighbours of the pair by
-        // shuffles (odd cell of the lane to the left, even cell of the one to
-        // the right), halo densities at the strip ends
-        R wl = __shfl_up_sync(FULL, r0.y, 1), er = __shfl_down_sync(FULL, r0.x, 1);
-        if (lane == 0) wl = hl0;
-        if (lane == 31) er = hr0;
-        F2 re = f2(r0.y, er), rw = f2(wl, r0.x);
-        F2 rn = rp, rs = rm;
-        if (!FAST) {
-            // a missing neighbour (wall side, solid) takes the cell's own density
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const R own = comp(r0, k);
-                if (comp(re, k) < R(0)) comp(re, k) = own;
-                if (comp(rw, k) < R(0)) comp(rw, k) = own;
-                if (comp(rn, k) < R(0)) comp(rn, k) = own;
-                if (comp(rs, k) < R(0)) comp(rs, k) = own;
-            }
-        }
-        F2 Fx = f2(0.f), Fy = f2(0.f);
-        if (FORCED) {
-            Fx = ld(p.c2.Fx);
-            Fy = ld(p.c2.Fy);
-            if (p.force) {
-                const size_t i = (size_t)y * p.pitch + xe;
-                const float2 fx2 = __ldg(reinterpret_cast<const float2 *>(p.force + i));
-                const float2 fy2 = __ldg(reinterpret_cast<const float2 *>(p.force + plane + i));
-                Fx = f2(fx2.x, fx2.y);
-                Fy = f2(fy2.x, fy2.y);
-            }
-        }
-        F2 out[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) out[a] = cur[a];
-        const F2 half = ld(p.c2.half);
-        collide_x2<MODE, FORCED, GUARD>(out, half * (re - rw), half * (rn - rs), Fx, Fy, p.c2, p.guard != 0,
-                                        p.guard_count);
-        if (!FAST && cur_valid != 3) {
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                if (!(cur_valid >> k & 1)) {
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) comp(out[a], k) = 0.f;
+                for (int k = 0; k < 2; ++k) {
+                    const R own = comp(r0, k);
+                    if (comp(re, k) < R(0)) comp(re, k) = own;
+                    if (comp(rw, k) < R(0)) comp(rw, k) = own;
+                    if (comp(rn, k) < R(0)) comp(rn, k) = own;
+                    if (comp(rs, k) < R(0)) comp(rs, k) = own;
                 }
-        }
-        // 2-wide stores of the row (x0 + SW <= pitch: the odd cell past nx, if
-        // any, lands in the row padding)
-        ST *fo = fout + (size_t)y * p.pitch + xe;
-        if constexpr (StorageTraits<ST>::kReduced) {
-            // one store path for both rounding modes (no cold alternative in the loop)
-            const uint32_t h = mix32(seed ^ (uint32_t)(y * p.nx + xe));  // one hash per pair of cells
+            }
+            F2 Fx = f2(0.f), Fy = f2(0.f);
+            if (FORCED) {
+                Fx = ld(p.c2.Fx);
+                Fy = ld(p.c2.Fy);
+                if (p.force) {
+                    const size_t i = (size_t)y * p.pitch + xe;
+                    const float2 fx2 = __ldg(reinterpret_cast<const float2 *>(p.force + i));
+                    const float2 fy2 = __ldg(reinterpret_cast<const float2 *>(p.force + plane + i));
+                    Fx = f2(fx2.x, fx2.y);
+                    Fy = f2(fy2.x, fy2.y);
+                }
+            }
+            F2 out[9];
 #pragma unroll
-            for (int a = 0; a < 9; ++a)
-                IO::stg2_sr(fo + a * plane, out[a], sround ? sr_bits(h, a) : IO::HALF_ULP);
-        } else {
+            for (int a = 0; a < 9; ++a) out[a] = cur[a];
+            const F2 half = ld(p.c2.half);
+            collide_x2<MODE, FORCED, GUARD>(out, half * (re - rw), half * (rn - rs), Fx, Fy, p.c2, p.guard != 0,
+                                            p.guard_count);
+            if (!FAST && cur_valid != 3) {
 #pragma unroll
-            for (int a = 0; a < 9; ++a) IO::stg2(fo + a * plane, out[a]);
+                for (int k = 0; k < 2; ++k)
+                    if (!(cur_valid >> k & 1)) {
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) comp(out[a], k) = 0.f;
+                    }
+            }
+            // 2-wide stores of the row (x0 + SW <= pitch: the odd cell past nx, if
+            // any, lands in the row padding)
+            ST *fo = fout + (size_t)y * p.pitch + xe;
+            if constexpr (StorageTraits<ST>::kReduced) {
+                // one store path for both rounding modes (no cold alternative in the loop)
+                const uint32_t h = mix32(seed ^ (uint32_t)(y * p.nx + xe));  // one hash per pair of cells
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+                    IO::stg2_sr(fo + a * plane, out[a], sround ? sr_bits(h, a) : IO::HALF_ULP);
+            } else {
+#pragma unroll
+                for (int a = 0; a < 9; ++a) IO::stg2(fo + a * plane, out[a]);
+            }
         }
 #pragma unroll
         for (int a = 0; a < 9; ++a) cur[a] = nxt[a];
