@@ -448,9 +448,9 @@ lbm_status autotune(lbm_batch *b)
         }
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
+        std::lock_guard<std::mutex> lk(b->mu);
         b->launches += reps;
         b->cell_updates += cells * reps;
-        std::lock_guard<std::mutex> lk(b->mu);
         for (int k = 0; k < b->max_slots; ++k)
             if (b->slots[k].used && b->slots[k].running) b->records[b->slots[k].id].steps += reps;
         if (ms < best_ms) {
@@ -531,11 +531,11 @@ lbm_status tick(lbm_batch *b, bool *busy)
         cudaMemset(b->d_work, 0, 2 * sizeof(unsigned int));
         return bfail(LBM_ERR_CUDA, "a batched step kernel's bounded wait expired");
     }
+    const double t = seconds(b);
+    std::lock_guard<std::mutex> lk(b->mu);  // counters and records are read by other threads
     b->launches += b->check_every;
     b->cell_updates += cells * b->check_every;
     b->ticks += 1;
-    const double t = seconds(b);
-    std::lock_guard<std::mutex> lk(b->mu);
     for (int i = 0; i < n; ++i) {
         const int k = b->h_active[i];
         Slot &s = b->slots[k];
@@ -690,6 +690,8 @@ lbm_status lbm_batch_submit(lbm_batch *b, const lbm_request *req, long *id)
         return bfail(LBM_ERR_INVALID, "request larger than the batch budget");
     {
         std::lock_guard<std::mutex> lk(b->mu);
+        // an engine thread that stopped on an error admits nothing any more
+        if (!b->engine_error.empty()) return bfail(LBM_ERR_CUDA, "batch engine stopped: " + b->engine_error);
         q.id = b->next_id++;
         Record &rec = b->records[q.id];
         rec.t_submit = seconds(b);
