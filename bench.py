@@ -12,6 +12,13 @@ scaling is weak.  Inputs (1.2 GB of populations per replica) exceed the 129 MB
 L2, so no L2 flush is needed between steps.
 
 --impl reference times the FP64 CPU oracle on the host cores instead.
+
+Other workloads (--workload, each prints its own JSON line): batch (steady
+solves/s of the seeded cavity set, FP16 batch against the plain FP32 solver one
+domain at a time), serve (a Poisson stream of steady-solve requests into the
+batch engine: latency percentiles, aggregate MLUPS), precision (storage formats
+to steady state on a scaled obstacle channel, against FP64 storage), gamma
+(steps to steady state per preconditioning parameter).
 """
 from __future__ import annotations
 
