@@ -82,6 +82,25 @@ def test_batch_domains_match_oracle(gi_mode):
     b.close()
 
 
+@pytest.mark.parametrize("storage,tol", [(lbm.STORAGE_F64, 1e-11), (lbm.STORAGE_BF16, 5e-3)])
+def test_batch_other_storages_match_oracle(storage, tol):
+    """The mixed batch in FP64 storage (the one-cell batch kernel; FP64
+    arithmetic, so tight) and in BF16 storage (8-bit mantissa deviations with
+    stochastic rounding, so loose): 100 steps, fields against the oracle."""
+    cases = mixed_cases()
+    b = lbm.Batch(1 << 30, storage=storage)
+    b.set_option("check_every", 50)
+    b.set_option("rows_per_item", 8)
+    _, fields = run_fixed(b, cases, 100)
+    for c, (rg, ug, vg) in zip(cases, fields):
+        ro, uo, vo = oracle_at(c, 100)
+        m = fluid(c)
+        err = max(np.abs(rg - ro)[m].max(), np.abs(ug - uo)[m].max(), np.abs(vg - vo)[m].max())
+        print("batch storage", storage, c.name, "max field error", err)
+        assert err < tol, (c.name, err)
+    b.close()
+
+
 def test_domain_result_independent_of_batch_mix():
     """A cavity stepped alone, in a mix of forced and unforced domains, and with
     another tile height: bitwise the same (one kernel, per-cell arithmetic that
