@@ -35,7 +35,9 @@
  *     rho; a missing neighbour (wall side or solid) takes the cell's own rho;
  *   - strain-rate guard (optional, off by default): if |D| < 0.1 |D0| the
  *     velocity-dependent parts P, Q, P~, Q~ are dropped for that cell.
- *     Parity unpinned (the paper is silent); it is counted, never silent.
+ *     Parity unpinned against the paper (it is silent on the case); the
+ *     trigger and the reduced solve are pinned to this reading by a property
+ *     test.  It is counted, never silent.
  */
 #include "gi_oracle.h"
 

@@ -288,6 +288,43 @@ def test_strain_solve_u0_closed_form():
     assert np.isclose(duy, -m3 / (2 * a) + m4 / (2 * b), rtol=1e-13)
 
 
+def test_strain_solve_guard_reading():
+    """The optional guard (the paper is silent on a vanishing determinant of
+    Eqs. 51-52): it fires exactly when |D| < 0.1 |D0|, D from Eq. 53 and D0 its
+    u = 0 value; then the solve is the u = 0 closed form applied to R3, R4 of
+    Eq. 54 (the density-gradient terms stay); otherwise the guarded solve is the
+    unguarded one."""
+    rng = np.random.default_rng(12)
+    fired = kept = 0
+    for _ in range(4000):
+        g = rng.uniform(0.15, 1.0)
+        rho = rng.uniform(0.95, 1.05)
+        ux, uy = rng.uniform(-0.3, 0.3, 2)
+        w3, w4 = rng.uniform(0.4, 1.9, 2)
+        m3, m4, drx, dry = rng.normal(scale=1e-3, size=4)
+        A, B, C = 4 / g**2 - 1 / g, 1 / g**2 - 1 / g, 1 / g - 1
+        a, b = 2 * rho / (3 * w3), 2 * rho / (3 * w4)
+        c1 = a - 0.5 * rho * (A * ux**2 + B * uy**2)
+        c2 = a - 0.5 * rho * (A * uy**2 + B * ux**2)
+        c1t = b - 0.5 * rho * (A * ux**2 - B * uy**2)
+        c2t = b - 0.5 * rho * (A * uy**2 - B * ux**2)
+        D, D0 = -c1 * c2t - c1t * c2, -2 * a * b
+        if abs(abs(D) - 0.1 * abs(D0)) < 1e-9 * abs(D0):
+            continue  # too close to the threshold to call
+        dux, duy, guarded = orc.strain_rates(rho, ux, uy, g, w3, w4, m3, m4, drx, dry, guard=True)
+        assert guarded == (abs(D) < 0.1 * abs(D0))
+        if guarded:
+            fired += 1
+            R3 = m3 - C / 3 * (ux * drx + uy * dry)
+            R4 = m4 - C / 3 * (ux * drx - uy * dry)
+            assert np.isclose(dux, -R3 / (2 * a) - R4 / (2 * b), rtol=1e-12, atol=1e-18)
+            assert np.isclose(duy, -R3 / (2 * a) + R4 / (2 * b), rtol=1e-12, atol=1e-18)
+        else:
+            kept += 1
+            assert (dux, duy) == orc.strain_rates(rho, ux, uy, g, w3, w4, m3, m4, drx, dry)[:2]
+    assert fired > 20 and kept > 20, (fired, kept)
+
+
 def test_strain_recovers_chapman_enskog_nonequilibrium():
     """A population set built with the Eq. 29/30 + Eq. 44 non-equilibrium part for a
     known strain returns that strain (m^(1) = -(2rho/3w)(div) + (w/2)E)."""
