@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=list(STORAGE_CODE), default="f32")
-    ap.add_argument("--n", type=int, default=4096, help="cavity side")
+    ap.add_argument("--n", "--side", dest="n", type=int, default=4096,
+                    help="cavity side (--side also under torchrun, whose parser takes --n as an abbreviation)")
     ap.add_argument("--gamma", type=float, default=0.5)
     ap.add_argument("--Re", type=float, default=1000.0)
     ap.add_argument("--gi-mode", type=int, default=2)
@@ -171,6 +172,23 @@ def dist_setup(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x, dist, device):
+    """The job's time is its slowest rank's: the max of a per-rank float over
+    all ranks (the value itself when there is one rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(cells_per_rank, steps, world, seconds):
+    """Whole-job cell updates per second (MLUPS): every rank advances its own
+    replica for the same number of steps (weak scaling)."""
+    return cells_per_rank * steps * world / seconds / 1e6
 
 
 def cpu_baseline(case_fn, seconds_target=15.0):
@@ -564,13 +582,9 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = g.kernel_launches - l0
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     cells = case.cells
-    value = cells * args.steps * world / (ms / 1e3) / 1e6
+    value = job_mlups(cells, args.steps, world, ms / 1e3)
     per_launch_s = ms / 1e3 / args.steps
     bpc = BYTES_PER_CELL[args.storage]
     achieved = bpc * cells / per_launch_s / 1e9
@@ -606,13 +620,9 @@ def main():
         g2.residual()
     g2.fields(out=outs)
     t1 = time.perf_counter()
-    e2e_s = t1 - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(t1 - t0, dist, "cuda")
     field_bytes = 3 * cells * 8
-    e2e = {"value": cells * e2e_steps * world / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": job_mlups(cells, e2e_steps, world, e2e_s), "unit": "MLUPS",
            "h2d_bytes_per_step": field_bytes / e2e_steps,
            "d2h_bytes_per_step": (field_bytes + nchunks * 40) / e2e_steps,
            "calls": f"lbm_init_fields + {nchunks} x (lbm_step({ce}) + lbm_residual) + lbm_fields, pinned host arrays"}
