@@ -81,6 +81,7 @@ def lib():
             L.orc_steps_done.argtypes = [ctypes.c_void_p]
             L.orc_guard_count.restype = ctypes.c_long
             L.orc_guard_count.argtypes = [ctypes.c_void_p]
+            L.orc_density_gradient_field.argtypes = [ctypes.c_void_p] * 4
             L.orc_set_threads.argtypes = [ctypes.c_int]
             L.orc_get_threads.restype = ctypes.c_int
             L.orc_lattice.argtypes = [ctypes.c_void_p] * 4
@@ -186,6 +187,13 @@ class Domain:
         f = np.empty((9, self.ny, self.nx))
         lib().orc_get_pops(self._h, _dp(f))
         return f
+
+    def density_gradient(self, rho):
+        """The domain's density-gradient stencil applied to rho (ny, nx)."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ny, self.nx)
+        gx, gy = np.empty((self.ny, self.nx)), np.empty((self.ny, self.nx))
+        lib().orc_density_gradient_field(self._h, _dp(rho), _dp(gx), _dp(gy))
+        return gx, gy
 
     def set_pops(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny, self.nx)

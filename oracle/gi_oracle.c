@@ -460,6 +460,21 @@ static void density_gradient(const orc_domain *d, int x, int y, double *drx, dou
     }
 }
 
+/* The density-gradient stencil alone (Eq. 54's d_i rho; central differences or
+ * the isotropic stencil, by the domain's fd_scheme, with the ghost rule of
+ * rho_neighbour), applied to a given density field rho[ny][nx] so that it can
+ * be checked against closed forms.  Overwrites the domain's post-streaming
+ * density scratch (the next step recomputes it). */
+void orc_density_gradient_field(orc_domain *d, const double *rho, double *gx, double *gy)
+{
+    memcpy(d->rho, rho, d->N * sizeof(double));
+    for (int y = 0; y < d->p.ny; ++y)
+        for (int x = 0; x < d->p.nx; ++x) {
+            const long i = (long)y * d->p.nx + x;
+            density_gradient(d, x, y, gx + i, gy + i);
+        }
+}
+
 void orc_step(orc_domain *d, long n)
 {
     const int nx = d->p.nx, ny = d->p.ny;

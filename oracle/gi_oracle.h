@@ -74,6 +74,7 @@ void   orc_destroy(orc_domain *d);
 int    orc_set_force_field(orc_domain *d, const double *Fx, const double *Fy);
 void   orc_init_equilibrium(orc_domain *d, const double *rho, const double *ux, const double *uy);
 void   orc_step(orc_domain *d, long n);
+void   orc_density_gradient_field(orc_domain *d, const double *rho, double *gx, double *gy);
 void   orc_get_pops(const orc_domain *d, double *f);
 void   orc_set_pops(orc_domain *d, const double *f);
 void   orc_fields(const orc_domain *d, double *rho, double *ux, double *uy);

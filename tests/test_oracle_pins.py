@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
+import workloads as wl
 
 EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
 EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
@@ -352,3 +353,54 @@ def test_source_moments_are_moments_of_source():
     S = orc.pops_from_raw(orc.source_moments(1e-3, -2e-3, 0.05, 0.02, 0.4))
     assert abs(S.sum()) < 1e-18
     assert np.isclose(np.dot(S, EX), 1e-3 / 0.4) and np.isclose(np.dot(S, EY), -2e-3 / 0.4)
+
+
+def _gradient(nx, ny, sides, fd, rho, solid=None):
+    d = orc.Domain(nx, ny, 0.05, 0.5, sides, fd=fd, solid=solid)
+    return d.density_gradient(rho)
+
+
+def test_density_gradient_stencils_on_a_periodic_mode():
+    """rho = 1 + a cos(kx) cos(qy) on a periodic box.  Central differences give
+    d_x rho = -a sin k sin(kx) cos(qy) (and the mirror for y); the isotropic
+    stencil 3 sum_a w_a e_a rho(x + e_a) named in Sec. 5 multiplies that by
+    (2 + cos q) / 3, since its diagonal neighbours average over y +- 1."""
+    nx, ny, a = 24, 20, 0.01
+    k, q = 2 * np.pi * 3 / nx, 2 * np.pi * 2 / ny
+    x, y = np.arange(nx)[None, :], np.arange(ny)[:, None]
+    rho = 1 + a * np.cos(k * x) * np.cos(q * y)
+    ex = -a * np.sin(k) * np.sin(k * x) * np.cos(q * y)
+    ey = -a * np.sin(q) * np.cos(k * x) * np.sin(q * y)
+    gx, gy = _gradient(nx, ny, wl.periodic_sides(), orc.FD_CENTRAL, rho)
+    assert np.abs(gx - ex).max() < 1e-16 and np.abs(gy - ey).max() < 1e-16
+    gx, gy = _gradient(nx, ny, wl.periodic_sides(), orc.FD_ISOTROPIC, rho)
+    assert np.abs(gx - ex * (2 + np.cos(q)) / 3).max() < 1e-16
+    assert np.abs(gy - ey * (2 + np.cos(k)) / 3).max() < 1e-16
+
+
+def test_density_gradient_ghost_rule():
+    """rho = 1 + b x + c y.  Inside, both stencils are exact (b, c).  A missing
+    neighbour (beyond a wall, or solid) takes the cell's own density: on the west
+    wall both give d_x rho = b/2, while d_y rho is c (central) and 5c/6
+    (isotropic: the two missing diagonals); at the south-west corner the
+    isotropic stencil gives ((5b + c)/12, (5c + b)/12) and central (b/2, c/2); east
+    of a lone solid cell the isotropic stencil gives (2b/3, c)."""
+    nx, ny, b, c = 12, 10, 0.003, -0.002
+    x, y = np.arange(nx)[None, :], np.arange(ny)[:, None]
+    rho = 1 + b * x + c * y
+    walls = ((wl.WALL, 0.0, 0.0),) * 4
+    gxc, gyc = _gradient(nx, ny, walls, orc.FD_CENTRAL, rho)
+    gxi, gyi = _gradient(nx, ny, walls, orc.FD_ISOTROPIC, rho)
+    inner = (slice(1, ny - 1), slice(1, nx - 1))
+    for g, v in ((gxc, b), (gyc, c), (gxi, b), (gyi, c)):
+        assert np.allclose(g[inner], v, rtol=1e-12, atol=0)
+    west = (slice(1, ny - 1), 0)
+    assert np.allclose(gxc[west], b / 2, rtol=1e-12) and np.allclose(gyc[west], c, rtol=1e-12)
+    assert np.allclose(gxi[west], b / 2, rtol=1e-12) and np.allclose(gyi[west], 5 * c / 6, rtol=1e-12)
+    assert np.isclose(gxc[0, 0], b / 2, rtol=1e-12) and np.isclose(gyc[0, 0], c / 2, rtol=1e-12)
+    assert np.isclose(gxi[0, 0], (5 * b + c) / 12, rtol=1e-12)
+    assert np.isclose(gyi[0, 0], (5 * c + b) / 12, rtol=1e-12)
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[5, 5] = 1
+    gxs, gys = _gradient(nx, ny, walls, orc.FD_ISOTROPIC, rho, solid=solid)
+    assert np.isclose(gxs[5, 6], 2 * b / 3, rtol=1e-12) and np.isclose(gys[5, 6], c, rtol=1e-12)
