@@ -93,6 +93,11 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U,
  *   "fx", "fy"  uniform body force (default 0)
  *   "guard"     1 = drop the velocity-dependent parts of the strain-rate solve
  *               where |D| < 0.1 |D0| (Eqs. 53-55; off by default), counted
+ *   "fd"        density gradient of the GI correction (Eq. 54): 0 (default)
+ *               central differences, 1 the isotropic stencil
+ *               d_i rho = 3 sum_a w_a e_ai rho(x + e_a) (Sec. 5 names both; a
+ *               missing neighbour takes the cell's own density either way);
+ *               single-domain contexts only (batches use central differences)
  *   "cells_per_item" rows per work item of the step kernel (tuning; >= 1)
  *   "stochastic_rounding" FP16/BF16 storage: 1 (default) rounds each stored
  *               deviation up or down with probability given by its distance

@@ -71,6 +71,7 @@ struct lbm_ctx {
     int gi_mode = LBM_GI_FULL;
     int storage = LBM_STORAGE_F32;
     int guard = 0;
+    int fd_iso = 0;  // density gradient: 0 central differences, 1 isotropic stencil
     int sround = 1;  // 16-bit storage: stochastic rounding of the stored deviations
     lbm_side sides[4];
     double Fx = 0, Fy = 0;
@@ -122,6 +123,7 @@ StepParams make_params(const lbm_ctx *c)
     p.pery = c->sides[2].kind == LBM_SIDE_PERIODIC;
     p.gi_mode = c->gi_mode;
     p.guard = c->guard;
+    p.fd_iso = c->fd_iso;
     p.sround = c->sround;
     p.step = (unsigned int)c->steps;
     p.gamma = c->gamma;
@@ -439,6 +441,9 @@ lbm_status lbm_set_option(lbm_ctx *c, const char *key, double v)
         c->gi_mode = (int)v;
     } else if (k == "guard") {
         c->guard = v != 0.0;
+    } else if (k == "fd") {
+        if (v != 0.0 && v != 1.0) return fail(LBM_ERR_INVALID, "fd must be 0 (central) or 1 (isotropic)");
+        c->fd_iso = (int)v;
     } else if (k == "stochastic_rounding") {
         c->sround = v != 0.0;
     } else if (k == "fx" || k == "fy") {
@@ -492,6 +497,7 @@ lbm_status lbm_get_option(lbm_ctx *c, const char *key, double *v)
     if (k.size() == 6 && k.compare(0, 5, "omega") == 0 && k[5] >= '3' && k[5] <= '8') *v = c->omega[k[5] - '0'];
     else if (k == "gi_mode") *v = c->gi_mode;
     else if (k == "guard") *v = c->guard;
+    else if (k == "fd") *v = c->fd_iso;
     else if (k == "stochastic_rounding") *v = c->sround;
     else if (k == "fx") *v = c->Fx;
     else if (k == "fy") *v = c->Fy;

@@ -124,6 +124,7 @@ struct StepParams {
     int perx, pery;         // periodic in x / y
     int gi_mode;            // LBM_GI_*
     int guard;              // strain-solve guard on/off
+    int fd_iso;             // density gradient: isotropic stencil (nonzero) or central differences
     // relaxation and preconditioning constants
     double gamma;
     double w3, w4, w5, w6, w7, w8;

@@ -11,7 +11,8 @@
 // mbarrier per slot.  Each source element crosses HBM once per step and several
 // rows are in flight per warp; the pulls of Eq. 2b are shared-memory loads.
 //
-// Density gradient (same time level, central differences): each lane keeps the
+// Density gradient (same time level, central differences, or the isotropic
+// stencil 3 sum_a w_a e_a rho(x + e_a) as a variant): each lane keeps the
 // post-streaming density of its column for rows y - 1, y, y + 1 in registers;
 // the x neighbours come from the adjacent lanes by shuffles, and the halo
 // columns x0 - 1 and x0 + WS from a lane-parallel pull.  Density entries are -1 for
@@ -177,7 +178,7 @@ __device__ __forceinline__ void warp_begin(WarpCtx &w, unsigned char *smem)
 // One work item: rows [seg*Ly, ...) of the 32-column strip `strip` of the
 // domain described by p, reading fin through tin and writing through tout.
 // Returns false when a bounded wait expired (the caller then stops).
-template <typename ST, int MODE, bool FORCED>
+template <typename ST, int MODE, bool FORCED, bool ISO = false>
 __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const CUtensorMap *tin,
                                          const CUtensorMap *tout, const ST *__restrict__ fin, int strip, int seg,
                                          uint32_t step)
@@ -426,6 +427,7 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
         };
         produce_any(y0 - 1, nxt, nxt_valid, rm, d0, d1);
         produce_any(y0, cur, cur_valid, r0, hl0, hr0);
+        R hlm = d0, hrm = d1;  // halo densities of row y - 1 (isotropic gradient only)
         __syncwarp();
         if (lane == 0) {
             // source row y0 - 2 is no longer read: refill its slot
@@ -447,17 +449,49 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
                 if (issued <= kmax) fence_proxy_async();
                 while (issued <= kmax) issue(issued++);
             }
-            // density gradient by central differences (x neighbours by shuffles)
+            // density gradient (x neighbours by shuffles; the isotropic stencil
+            // takes the diagonal neighbours from rows y - 1 and y + 1 the same way)
             R re = __shfl_down_sync(FULL, r0, 1), rw = __shfl_up_sync(FULL, r0, 1);
             if (lane == 31) re = hr0;
             if (lane == 0) rw = hl0;
             R rn = rp, rs = rm;
+            R rne = rp, rnw = rp, rse = rm, rsw = rm;
+            if constexpr (ISO) {
+                rne = __shfl_down_sync(FULL, rp, 1);
+                rnw = __shfl_up_sync(FULL, rp, 1);
+                rse = __shfl_down_sync(FULL, rm, 1);
+                rsw = __shfl_up_sync(FULL, rm, 1);
+                if (lane == 31) {
+                    rne = hrp;
+                    rse = hrm;
+                }
+                if (lane == 0) {
+                    rnw = hlp;
+                    rsw = hlm;
+                }
+            }
             if (!FAST) {
                 // a missing neighbour (wall side, solid) takes the cell's own density
                 re = re < R(0) ? r0 : re;
                 rw = rw < R(0) ? r0 : rw;
                 rn = rn < R(0) ? r0 : rn;
                 rs = rs < R(0) ? r0 : rs;
+                if constexpr (ISO) {
+                    rne = rne < R(0) ? r0 : rne;
+                    rnw = rnw < R(0) ? r0 : rnw;
+                    rse = rse < R(0) ? r0 : rse;
+                    rsw = rsw < R(0) ? r0 : rsw;
+                }
+            }
+            R drx, dry;
+            if constexpr (ISO) {
+                // d_i rho = 3 sum_a w_a e_ai rho(x + e_a): a third of the axis
+                // differences plus a twelfth of the diagonal ones
+                drx = (re - rw) / R(3) + ((rne + rse) - (rnw + rsw)) / R(12);
+                dry = (rn - rs) / R(3) + ((rne + rnw) - (rse + rsw)) / R(12);
+            } else {
+                drx = R(0.5) * (re - rw);
+                dry = R(0.5) * (rn - rs);
             }
             R Fx = R(0), Fy = R(0);
             if (FORCED) {
@@ -472,8 +506,7 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
             R out[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) out[a] = cur[a];
-            collide_cell<R, MODE, FORCED>(out, R(0.5) * (re - rw), R(0.5) * (rn - rs), Fx, Fy, c, p.guard != 0,
-                                          p.guard_count);
+            collide_cell<R, MODE, FORCED>(out, drx, dry, Fx, Fy, c, p.guard != 0, p.guard_count);
             // stage the row (the previous row's store must have read the buffer)
             if (lane == 0) bulk_wait_read_0();
             __syncwarp();
@@ -499,6 +532,10 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
             cur_valid = nxt_valid;
             rm = r0;
             r0 = rp;
+            if constexpr (ISO) {
+                hlm = hl0;
+                hrm = hr0;
+            }
             hl0 = hlp;
             hr0 = hrp;
             return true;
@@ -554,8 +591,9 @@ __device__ __forceinline__ int next_item(const WarpCtx &w, unsigned int *work)
     return __shfl_sync(0xffffffffu, it, 0);
 }
 
-// One time step of one domain.
-template <typename ST, int MODE, bool FORCED>
+// One time step of one domain (ISO: the variant with the isotropic
+// density-gradient stencil).
+template <typename ST, int MODE, bool FORCED, bool ISO = false>
 __global__ void __launch_bounds__(THREADS, MinBlocks<ST>::value)
 stream_collide_kernel(const __grid_constant__ StepParams p, const __grid_constant__ CUtensorMap tin,
                       const __grid_constant__ CUtensorMap tout, const ST *__restrict__ fin)
@@ -565,7 +603,7 @@ stream_collide_kernel(const __grid_constant__ StepParams p, const __grid_constan
     warp_begin<ST>(w, smem);
     bool abort = false;
     for (int item = next_item(w, p.work); item < p.nitems; item = next_item(w, p.work)) {
-        if (!run_item<ST, MODE, FORCED>(w, p, &tin, &tout, fin, item % p.nstrips, item / p.nstrips, p.step)) {
+        if (!run_item<ST, MODE, FORCED, ISO>(w, p, &tin, &tout, fin, item % p.nstrips, item / p.nstrips, p.step)) {
             abort = true;
             break;
         }
@@ -678,6 +716,12 @@ cudaError_t launch_step_t(const StepParams &p, const CUtensorMap &tin, const CUt
     const ST *in = static_cast<const ST *>(fin);
     const bool forced = p.force != nullptr || p.Fx != 0.0 || p.Fy != 0.0;
 #define LBM_LAUNCH(M, F) stream_collide_kernel<ST, M, F><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, tout, in)
+    if (p.fd_iso && p.gi_mode == LBM_GI_FULL) {
+        // the density gradient enters the full kernel only
+        if (forced) stream_collide_kernel<ST, LBM_GI_FULL, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, tout, in);
+        else stream_collide_kernel<ST, LBM_GI_FULL, false, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, tout, in);
+        return cudaGetLastError();
+    }
     switch (p.gi_mode) {
     case LBM_GI_UNCORRECTED:
         if (forced) LBM_LAUNCH(LBM_GI_UNCORRECTED, true);
@@ -696,11 +740,11 @@ cudaError_t launch_step_t(const StepParams &p, const CUtensorMap &tin, const CUt
     return cudaGetLastError();
 }
 
-template <typename ST, int MODE, bool FORCED>
+template <typename ST, int MODE, bool FORCED, bool ISO = false>
 int blocks_per_sm_variant()
 {
     using T = Tile<ST>;
-    auto fn = stream_collide_kernel<ST, MODE, FORCED>;
+    auto fn = stream_collide_kernel<ST, MODE, FORCED, ISO>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM_BYTES) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -727,7 +771,13 @@ int blocks_per_sm_t(int gi_mode, bool forced)
     switch (gi_mode) {
     case LBM_GI_UNCORRECTED: return blocks_per_sm_mode<ST, LBM_GI_UNCORRECTED>(forced);
     case LBM_GI_CUBIC_ONLY: return blocks_per_sm_mode<ST, LBM_GI_CUBIC_ONLY>(forced);
-    default: return blocks_per_sm_mode<ST, LBM_GI_FULL>(forced);
+    default: {
+        // the isotropic-gradient variant gets its shared-memory attribute too
+        const int a = blocks_per_sm_mode<ST, LBM_GI_FULL>(forced);
+        const int i = forced ? blocks_per_sm_variant<ST, LBM_GI_FULL, true, true>()
+                             : blocks_per_sm_variant<ST, LBM_GI_FULL, false, true>();
+        return a < i ? a : i;
+    }
     }
 }
 

@@ -174,7 +174,7 @@ __device__ __forceinline__ void warp_end_x2(WarpCtx &w, bool abort, int *error, 
 // One work item: rows [seg*Ly, ...) of the 64-column strip `strip` of the
 // domain described by p, reading fin through tin (wide load box) and writing
 // fout directly.  Returns false when a bounded wait expired.
-template <typename ST, int MODE, bool FORCED, bool GUARD = false>
+template <typename ST, int MODE, bool FORCED, bool GUARD = false, bool ISO = false>
 __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, const CUtensorMap *tin,
                                             const ST *__restrict__ fin, ST *__restrict__ fout, int strip, int seg,
                                             uint32_t step)
@@ -434,6 +434,7 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
     int cur_valid = 0, nxt_valid = 0;
     F2 rm = f2(-1.f), r0 = f2(-1.f), rp;
     R hl0 = R(-1), hr0 = R(-1), hlp, hrp;
+    R hlm = R(-1), hrm = R(-1);  // halo densities of row y - 1 (isotropic gradient only)
 #pragma unroll
     for (int a = 0; a < 9; ++a) cur[a] = f2(0.f);
     const size_t plane = (size_t)p.plane;
@@ -454,14 +455,32 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
             while (issued <= kmax) issue(issued++);
         }
         if (y >= y0) {  // the warm-up passes only produce
-            // density gradient by central differences: x neighbours of the pair by
-            // shuffles (odd cell of the lane to the left, even cell of the one to
-            // the right), halo densities at the strip ends
+            // density gradient: x neighbours of the pair by shuffles (odd cell of
+            // the lane to the left, even cell of the one to the right), halo
+            // densities at the strip ends; the isotropic stencil takes the
+            // diagonal neighbours from rows y - 1 and y + 1 the same way
             R wl = __shfl_up_sync(FULL, r0.y, 1), er = __shfl_down_sync(FULL, r0.x, 1);
             if (lane == 0) wl = hl0;
             if (lane == 31) er = hr0;
             F2 re = f2(r0.y, er), rw = f2(wl, r0.x);
             F2 rn = rp, rs = rm;
+            F2 rne = rp, rnw = rp, rse = rm, rsw = rm;
+            if constexpr (ISO) {
+                R wlp = __shfl_up_sync(FULL, rp.y, 1), erp = __shfl_down_sync(FULL, rp.x, 1);
+                R wlm = __shfl_up_sync(FULL, rm.y, 1), erm = __shfl_down_sync(FULL, rm.x, 1);
+                if (lane == 0) {
+                    wlp = hlp;
+                    wlm = hlm;
+                }
+                if (lane == 31) {
+                    erp = hrp;
+                    erm = hrm;
+                }
+                rne = f2(rp.y, erp);
+                rnw = f2(wlp, rp.x);
+                rse = f2(rm.y, erm);
+                rsw = f2(wlm, rm.x);
+            }
             if (!FAST) {
                 // a missing neighbour (wall side, solid) takes the cell's own density
 #pragma unroll
@@ -471,6 +490,12 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
                     if (comp(rw, k) < R(0)) comp(rw, k) = own;
                     if (comp(rn, k) < R(0)) comp(rn, k) = own;
                     if (comp(rs, k) < R(0)) comp(rs, k) = own;
+                    if constexpr (ISO) {
+                        if (comp(rne, k) < R(0)) comp(rne, k) = own;
+                        if (comp(rnw, k) < R(0)) comp(rnw, k) = own;
+                        if (comp(rse, k) < R(0)) comp(rse, k) = own;
+                        if (comp(rsw, k) < R(0)) comp(rsw, k) = own;
+                    }
                 }
             }
             F2 Fx = f2(0.f), Fy = f2(0.f);
@@ -488,9 +513,19 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
             F2 out[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) out[a] = cur[a];
-            const F2 half = ld(p.c2.half);
-            collide_x2<MODE, FORCED, GUARD>(out, half * (re - rw), half * (rn - rs), Fx, Fy, p.c2, p.guard != 0,
-                                            p.guard_count);
+            F2 drx, dry;
+            if constexpr (ISO) {
+                // d_i rho = 3 sum_a w_a e_ai rho(x + e_a): a third of the axis
+                // differences plus a twelfth of the diagonal ones
+                const F2 third = ld(p.c2.third), twelfth = f2(1.f / 12.f);
+                drx = fma2(twelfth, (rne + rse) - (rnw + rsw), third * (re - rw));
+                dry = fma2(twelfth, (rne + rnw) - (rse + rsw), third * (rn - rs));
+            } else {
+                const F2 half = ld(p.c2.half);
+                drx = half * (re - rw);
+                dry = half * (rn - rs);
+            }
+            collide_x2<MODE, FORCED, GUARD>(out, drx, dry, Fx, Fy, p.c2, p.guard != 0, p.guard_count);
             if (!FAST && cur_valid != 3) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k)
@@ -518,6 +553,10 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         cur_valid = nxt_valid;
         rm = r0;
         r0 = rp;
+        if constexpr (ISO) {
+            hlm = hl0;
+            hrm = hr0;
+        }
         hl0 = hlp;
         hr0 = hrp;
         return true;
@@ -543,8 +582,10 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
 }
 
 // One time step of one domain (GUARD: the variant with the strain-solve guard,
-// launched only when a context turns the guard on).
-template <typename ST, int MODE, bool FORCED, bool GUARD = false>
+// launched only when a context turns the guard on; ISO: the variant with the
+// isotropic density-gradient stencil, which carries the guard as well and
+// leaves it to the context's flag).
+template <typename ST, int MODE, bool FORCED, bool GUARD = false, bool ISO = false>
 __global__ void __launch_bounds__(THREADS, FORCED ? MIN_BLOCKS_BATCH_X2 : MIN_BLOCKS_X2)
 stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_constant__ CUtensorMap tin,
                          const ST *__restrict__ fin, ST *__restrict__ fout)
@@ -560,7 +601,7 @@ stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_cons
         const int phase = item / per, r = item - phase * per;
         const int strip = r % p.nstrips, seg = phase + (r / p.nstrips) * p.nwave;
         if (seg >= p.nseg) continue;
-        if (!run_item_x2<ST, MODE, FORCED, GUARD>(w, p, &tin, fin, fout, strip, seg, p.step)) {
+        if (!run_item_x2<ST, MODE, FORCED, GUARD, ISO>(w, p, &tin, fin, fout, strip, seg, p.step)) {
             abort = true;
             break;
         }
@@ -623,6 +664,12 @@ cudaError_t launch_step_x2_t(const StepParams &p, const CUtensorMap &tin, const 
     ST *out = static_cast<ST *>(fout);
     const bool forced = p.force != nullptr || p.Fx != 0.0 || p.Fy != 0.0;
 #define LBM_LAUNCH(M, F) stream_collide_x2_kernel<ST, M, F><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out)
+    if (p.fd_iso && p.gi_mode == LBM_GI_FULL) {
+        // the density gradient enters the full kernel only
+        if (forced) stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
+        else stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
+        return cudaGetLastError();
+    }
     if (p.guard && p.gi_mode == LBM_GI_FULL) {
         // the guard acts in the full kernel only (the strain solve)
         if (forced) stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
@@ -676,12 +723,16 @@ int blocks_per_sm_x2_t(int gi_mode, bool forced)
         return forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, true>, T::SMEM_BYTES)
                       : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, false>, T::SMEM_BYTES);
     default: {
-        // the guard variants get their shared-memory attribute too (min of both)
+        // the guard and isotropic-gradient variants get their shared-memory
+        // attribute too (min of all three)
         const int a = forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true>, T::SMEM_BYTES)
                              : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false>, T::SMEM_BYTES);
         const int b = forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true>, T::SMEM_BYTES)
                              : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true>, T::SMEM_BYTES);
-        return a < b ? a : b;
+        const int i = forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true, true>, T::SMEM_BYTES)
+                             : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true, true>, T::SMEM_BYTES);
+        const int ab = a < b ? a : b;
+        return ab < i ? ab : i;
     }
     }
 }

@@ -11,6 +11,8 @@ Tolerances (FP32 storage and collision): populations to 2e-6 absolute, and the
 spec bound max|du|/U <= 1e-5 after 1000 steps of the 128 x 128 cavity.
 FP64 storage: 1e-12.  FP16/BF16 storage: stated per test.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -41,9 +43,11 @@ def fluid(case):
     return np.ones((case.ny, case.nx), bool) if case.solid is None else case.solid == 0
 
 
-def compare(case, steps, gi_mode=orc.GI_FULL, storage=lbm.STORAGE_F32, pop_tol=2e-6, **opts):
+def compare(case, steps, gi_mode=orc.GI_FULL, storage=lbm.STORAGE_F32, pop_tol=2e-6, fd=orc.FD_CENTRAL, **opts):
+    if fd != orc.FD_CENTRAL:
+        opts["fd"] = fd
     g = lbm.solver_from_case(case, gi_mode=gi_mode, storage=storage, **opts)
-    o = oracle_for(case, gi_mode)
+    o = oracle_for(case, gi_mode, fd=fd)
     g.step(steps)
     o.step(steps)
     fg, fo = g.populations(), o.pops()
@@ -141,6 +145,36 @@ def test_obstacle_channel_with_uniform_force():
 def test_variable_force_field():
     c = wl.four_rolls_mill(64, 0.045, 20.0, 0.3)
     compare(c, 150)
+
+
+@pytest.mark.parametrize("storage,tol", [(lbm.STORAGE_F32, 2e-6), (lbm.STORAGE_F64, 1e-12)])
+def test_isotropic_density_gradient(storage, tol):
+    """Option "fd" = 1: the isotropic stencil 3 sum_a w_a e_a rho(x + e_a) for the
+    density gradient of Eq. 54, against the oracle's, on walls with a moving lid
+    (corners: diagonal neighbours beyond two sides), a ragged periodic domain
+    (strip seams and the periodic x patch) and an obstacle (the per-cell path,
+    diagonal neighbours inside the solid).  The inputs tell the stencils apart:
+    the oracle's own isotropic and central runs differ by far more than the
+    parity bound, so a GPU run that ignored the option would fail it."""
+    ob = wl.channel_obstacle(nx=260, ny=48, D=8, Re=20.0, U0=0.05, gamma=0.3, xc=60)
+    rnd = wl.random_periodic(260, 48, 0.3, ob.nu, seed=7)
+    ob = dataclasses.replace(ob, name=ob.name + "_rand7", rho0=rnd.rho0, ux0=rnd.ux0, uy0=rnd.uy0)
+    cases = [(wl.random_cavity_state(200, 37, 0.5, Re=80.0, seed=5), 120),
+             (wl.random_periodic(300, 41, 0.45, 0.03, seed=11), 60),
+             (ob, 100)]
+    apart = 0.0
+    for c, steps in cases:
+        compare(c, steps, storage=storage, pop_tol=tol, fd=orc.FD_ISOTROPIC)
+        oi, oc = oracle_for(c, fd=orc.FD_ISOTROPIC), oracle_for(c)
+        oi.step(steps)
+        oc.step(steps)
+        d = np.abs(oi.pops() - oc.pops())[:, fluid(c)].max()
+        print("isotropic vs central (oracle),", c.name, "max population difference", d)
+        apart = max(apart, d)
+    assert apart > 30 * tol, apart
+    g = lbm.solver_from_case(cases[0][0], storage=storage, fd=orc.FD_ISOTROPIC)
+    assert g.get_option("fd") == 1
+    g.close()
 
 
 def test_fp64_storage_matches_tightly():
