@@ -177,6 +177,27 @@ def test_isotropic_density_gradient(storage, tol):
     g.close()
 
 
+def test_hartmann_flow_matches_oracle_and_analytic():
+    """Hartmann flow (Sec. 6; the body force F_b Ha cosh(Ha z/L)/sinh(Ha) across a
+    walled channel, 70 x 40, Ha = 5, gamma = 0.1, Ma = 0.02): populations against
+    the oracle after 500 steps, then the profile after 8000 steps against the
+    oracle's steady profile (FP32 storage: 2e-5 of the centre-line speed) and,
+    like the oracle's (3.37 %), within 3.5 % (relative L2) of the printed analytic one."""
+    c = wl.hartmann(70, 40, 5.0)
+    compare(c, 500)
+    g = lbm.solver_from_case(c)
+    g.step(8000)
+    _, ug, vg = g.fields()
+    g.close()
+    o = oracle_for(wl.hartmann(4, 40, 5.0))
+    o.step(8000)
+    _, uo, _ = o.fields()
+    assert np.abs(ug - uo[:, :1]).max() < 2e-5 * c.U and np.abs(vg).max() < 2e-5 * c.U
+    ua = c.meta["ua"]
+    e = np.sqrt(((ug.mean(axis=1) - ua) ** 2).sum() / (ua ** 2).sum())
+    assert e < 3.5e-2, e
+
+
 def test_fp64_storage_matches_tightly():
     c = wl.random_cavity_state(150, 33, 0.4, Re=60.0, seed=2)
     compare(c, 80, storage=lbm.STORAGE_F64, pop_tol=1e-12)

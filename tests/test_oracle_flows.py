@@ -207,3 +207,35 @@ def test_four_rolls_mill_against_analytic():
         gu = np.sqrt(((u - ua) ** 2).sum() / (ua**2).sum())
         gv = np.sqrt(((v - va) ** 2).sum() / (va**2).sum())
         assert gu < 1e-2 and gv < 1e-2, (gi_mode, gu, gv)
+
+
+def _steady_profile(c, chunk=500, max_steps=100000):
+    d = make(c)
+    prev = None
+    for _ in range(max_steps // chunk):
+        d.step(chunk)
+        _, u, v = d.fields()
+        if prev is not None and np.abs(u - prev).max() <= 1e-14 * np.abs(u).max():
+            break
+        prev = u
+    assert np.abs(v).max() < 1e-12 * np.abs(u).max()
+    assert np.abs(u - u[:, :1]).max() < 1e-12 * np.abs(u).max()  # x-invariant
+    return u[:, 0]
+
+
+@pytest.mark.parametrize("Ha", [2.0, 5.0, 10.0])
+def test_hartmann_flow_against_analytic(Ha):
+    """Hartmann flow (Sec. 6, gamma = 0.1, Ma = 0.02): the body force
+    F_b Ha cosh(Ha z/L)/sinh(Ha) (driving force plus the Lorentz force of the
+    printed induced field) between walls at z = +-L.  The steady profile converges
+    to the printed analytic one, u_x = (F_b L^2/(Ha nu)) coth(Ha) [1 -
+    cosh(Ha z/L)/cosh(Ha)], at second order in the channel width (the
+    half-way bounce-back slip at tau = 3.5 sets the constant)."""
+    errs = []
+    for ny in (40, 80):
+        c = wl.hartmann(4, ny, Ha)
+        u = _steady_profile(c)
+        ua = c.meta["ua"]
+        errs.append(np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum()))
+    assert errs[1] < 2.5e-2, errs
+    assert 3.6 < errs[0] / errs[1] < 4.4, errs

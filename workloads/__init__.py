@@ -162,6 +162,26 @@ def four_rolls_mill(n: int = 251, u0: float = 0.045, Re: float = 20.0, gamma: fl
                 force_x=fx, force_y=fy, meta={"ua": ua, "va": va, "Re": Re})
 
 
+def hartmann(nx: int, ny: int, Ha: float, nu: float = 0.1, gamma: float = 0.1, Ma: float = 0.02) -> Case:
+    """Hartmann flow (Sec. 6): a channel periodic in x between stationary walls at
+    y = -1/2 and ny - 1/2 (half width L = ny/2, z = y + 1/2 - L), driven by a
+    driving force F_b plus the Lorentz force B0 dB_x/dz of the induced field
+    B_x(z) = (F_b L / B0)[sinh(Ha z/L)/sinh(Ha) - z/L], which together give the
+    body force F_x(z) = F_b Ha cosh(Ha z/L) / sinh(Ha).  Analytic steady profile
+    u_x(z) = (F_b L^2 / (Ha nu)) coth(Ha) [1 - cosh(Ha z/L) / cosh(Ha)]; F_b is
+    set so that the centre-line speed is Ma c_s."""
+    L = ny / 2.0
+    z = np.arange(ny, dtype=np.float64) + 0.5 - L
+    umax = Ma / np.sqrt(3.0)
+    Fb = umax * Ha * nu / (L * L / np.tanh(Ha) * (1.0 - 1.0 / np.cosh(Ha)))
+    fx = Fb * Ha * np.cosh(Ha * z / L) / np.sinh(Ha)
+    ua = Fb * L * L / (Ha * nu) / np.tanh(Ha) * (1.0 - np.cosh(Ha * z / L) / np.cosh(Ha))
+    sides = ((PERIODIC, 0.0, 0.0), (PERIODIC, 0.0, 0.0), (WALL, 0.0, 0.0), (WALL, 0.0, 0.0))
+    return Case(f"hartmann{nx}x{ny}_Ha{Ha:g}", nx, ny, nu, gamma, sides, U=umax,
+                force_x=np.broadcast_to(fx[:, None], (ny, nx)).copy(), force_y=np.zeros((ny, nx)),
+                meta={"ua": ua, "Ha": Ha, "Fb": Fb})
+
+
 def batch_cavities(count: int = 256, seed: int = 0, U: float = 0.1):
     """Independent cavities: side 64 + 32 k with k ~ U{0..30}, Re ~ U[100, 1000],
     gamma ~ U[0.2, 1.0]."""
