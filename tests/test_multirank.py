@@ -69,3 +69,17 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["steps"] == 2
     assert line["value"] > 0 and line["e2e"]["value"] == line["value"]
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_time_budget_bounds_the_sample():
+    """The reference arm stops its timed oracle steps at the time budget and says
+    how many of the requested steps it timed."""
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--side", "256", "--steps", "1000",
+           "--warmup", "1", "--reference-budget-s", "0.2"]
+    out = subprocess.run(cmd, cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="2"), capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["steps"] == 1000 and 1 <= line["steps_timed"] < 1000
+    assert line["cpu_baseline"]["sample"].startswith(f"{line['steps_timed']} of 1000 oracle steps")
+    assert line["value"] > 0
