@@ -4,6 +4,7 @@ import ctypes
 import glob
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -65,3 +66,48 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(lbm.LbmError) as e:
         lbm.Solver(16, 16, 0.1, 0.5, 0.1)
     assert e.value.status == lbm.ERR_CUDA
+
+
+def declared_prototypes():
+    """name -> parameter count of every function prototype in include/*.h."""
+    protos = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(lbm_\w+)\s*\(([^;{}]*?)\)\s*;", text):
+            params = m.group(2).strip()
+            protos[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return protos
+
+
+def test_binding_arity_matches_prototypes():
+    protos = declared_prototypes()
+    assert set(protos) == set(declared_functions())
+    for name, n in protos.items():
+        assert len(lbm.SIGNATURES[name][1]) == n, (name, n, lbm.SIGNATURES[name][1])
+
+
+STRUCTS = {"lbm_side": lbm.Side, "lbm_boundaries": lbm.Boundaries, "lbm_request": lbm.Request,
+           "lbm_result": lbm.Result, "lbm_population_desc": lbm.PopulationDesc, "lbm_allocator": lbm.Allocator}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets
+    (gcc on the header itself)."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbm.h"', "int main(void) {"]
+    for cname, py in STRUCTS.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines))
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in STRUCTS.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
