@@ -146,7 +146,12 @@ lbm_status lbm_steps_done(lbm_ctx *ctx, long *steps);
 lbm_status lbm_guard_count(lbm_ctx *ctx, long *count);
 
 /* Checkpoint: the stored post-collision array (in its storage format), step
- * count and parameters.  lbm_load needs a context of the same size. */
+ * count and parameters (storage format, gi_mode, gamma, nu, omega3..omega8,
+ * uniform force).  lbm_load needs a context of the same size; it restores
+ * those and keeps the context's own sides, solid mask, force field and the
+ * options "guard", "fd", "stochastic_rounding" and "cells_per_item".  Errors:
+ * LBM_ERR_IO for an unreadable, foreign or truncated file, LBM_ERR_INVALID
+ * for a size mismatch. */
 lbm_status lbm_save(lbm_ctx *ctx, const char *path);
 lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 
