@@ -8,7 +8,7 @@ density gradient), advances it once, and the window's interior must match the
 GPU's step n.
 
 Tolerances (FP32 storage and collision): populations to 2e-6 absolute, and the
-spec bound max|du|/U <= 1e-5 after 1000 steps of the 128 x 128 cavity.
+velocity bound max|du|/U <= 1e-5 after 1000 steps of the 128 x 128 cavity.
 FP64 storage: 1e-12.  FP16/BF16 storage: stated per test.
 """
 import dataclasses
@@ -73,7 +73,7 @@ def test_random_cavity_walls_and_lid(gi_mode):
     compare(c, 120, gi_mode)
 
 
-def test_cavity_128_1000_steps_north_star_bound():
+def test_cavity_128_1000_steps_velocity_bound():
     """128 x 128 lid-driven cavity, Re = 100, gamma = 0.5, from rest: after 1000
     steps max |du| / U <= 1e-5."""
     c = wl.cavity(128, 100.0, 0.1, 0.5)
