@@ -239,3 +239,41 @@ def test_hartmann_flow_against_analytic(Ha):
         errs.append(np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum()))
     assert errs[1] < 2.5e-2, errs
     assert 3.6 < errs[0] / errs[1] < 4.4, errs
+
+
+def test_residual_and_sums_closed_forms():
+    """Convergence residual and sums on states with known values.  A uniform
+    state rho0, (a, b) on an n x m periodic box has mass N rho0, momentum
+    N rho0 (a, b) and sum |u|^2 = N (a^2 + b^2); the snapshot starts at the
+    initial field (residual 0) and stays at rounding level while this fixed
+    point is stepped; replacing the state by the uniform (a', b') gives
+    ||u - u_snap|| / ||u|| = |(a', b') - (a, b)| / |(a', b')|.  Solid cells are
+    left out of every sum."""
+    n, m, rho0, a, b, a2, b2 = 12, 9, 1.02, 0.06, -0.035, -0.01, 0.045
+    N = n * m
+
+    def uniform(ux, uy):
+        return wl.Case("uniform", n, m, 0.02, 0.5, wl.periodic_sides(), rho0=np.full((m, n), rho0),
+                       ux0=np.full((m, n), ux), uy0=np.full((m, n), uy))
+
+    d = make(uniform(a, b))
+    r, s = d.residual()
+    assert r == 0.0 and s[0] == 0.0
+    assert np.isclose(s[1], N * (a * a + b * b), rtol=1e-13)
+    assert np.isclose(s[2], N * rho0, rtol=1e-14)
+    assert np.isclose(s[3], N * rho0 * a, rtol=1e-13) and np.isclose(s[4], N * rho0 * b, rtol=1e-13)
+    d.step(7)
+    r, _ = d.residual()
+    assert r < 1e-14
+    d.set_pops(make(uniform(a2, b2)).pops())
+    r, s = d.residual()
+    assert np.isclose(s[0], N * ((a2 - a) ** 2 + (b2 - b) ** 2), rtol=1e-12)
+    assert np.isclose(r, np.hypot(a2 - a, b2 - b) / np.hypot(a2, b2), rtol=1e-12)
+    # a walled box at rest with a solid block: only the fluid cells count
+    solid = np.zeros((m, n), np.uint8)
+    solid[3:6, 4:8] = 1
+    walls = ((wl.WALL, 0.0, 0.0),) * 4
+    c2 = wl.Case("solid", n, m, 0.02, 0.5, walls, solid=solid, rho0=np.full((m, n), rho0))
+    r, s = make(c2).residual()
+    assert np.isclose(s[2], (N - solid.sum()) * rho0, rtol=1e-14)
+    assert r == 0.0 and s[1] == 0.0
