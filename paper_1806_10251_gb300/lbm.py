@@ -19,6 +19,7 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_TIMEOUT
 SIDE_PERIODIC, SIDE_WALL, SIDE_MOVING_WALL = 0, 1, 2
 STORAGE_F32, STORAGE_F16, STORAGE_BF16, STORAGE_F64 = 0, 1, 2, 3
 GI_UNCORRECTED, GI_CUBIC_ONLY, GI_FULL = 0, 1, 2
+FD_CENTRAL, FD_ISOTROPIC = 0, 1  # values of the "fd" option (density-gradient stencil)
 
 _STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_DIVERGED",
            -5: "LBM_ERR_NOT_CONVERGED", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_IO"}
