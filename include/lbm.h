@@ -145,6 +145,17 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f);
 lbm_status lbm_steps_done(lbm_ctx *ctx, long *steps);
 lbm_status lbm_guard_count(lbm_ctx *ctx, long *count);
 
+/* Failure-path self-test (no counterpart in the paper).  Every mbarrier wait of
+ * the step kernels gives up after 2 s, raises the context's device error flag
+ * and lets its warp return; the next synchronising call then returns
+ * LBM_ERR_CUDA once, clears the flag and leaves the context usable.  This call
+ * drives that path without a fault: one thread of a one-block kernel waits,
+ * with the same bounded wait, on an mbarrier that nothing completes, and the
+ * call reports the raised flag like a step would.  Expected result:
+ * LBM_ERR_CUDA ("bounded wait expired"), *waited_s (optional) >= 2 s; LBM_OK
+ * would mean the wait did not expire.  The populations are not touched. */
+lbm_status lbm_bounded_wait_selftest(lbm_ctx *ctx, double *waited_s);
+
 /* Checkpoint: the stored post-collision array (in its storage format), step
  * count and parameters (storage format, gi_mode, gamma, nu, omega3..omega8,
  * uniform force).  lbm_load needs a context of the same size; it restores

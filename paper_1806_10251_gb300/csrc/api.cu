@@ -222,9 +222,11 @@ lbm_status check_device_error(lbm_ctx *c)
     cudaError_t e = cudaMemcpy(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error flag");
     if (v) {
-        cudaMemset(c->d_err, 0, sizeof(int));
-        cudaMemset(c->d_work, 0, 2 * sizeof(unsigned int));
-        return fail(LBM_ERR_CUDA, "a step kernel's bounded wait for its staged rows expired");
+        // on the context's stream: later kernels there see the cleared counters
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        cudaMemsetAsync(c->d_work, 0, 2 * sizeof(unsigned int), c->stream);
+        cudaStreamSynchronize(c->stream);
+        return fail(LBM_ERR_CUDA, "a kernel's bounded wait expired (device error flag raised)");
     }
     return LBM_OK;
 }
@@ -716,6 +718,20 @@ lbm_status lbm_guard_count(lbm_ctx *c, long *count)
     LBM_CUDA(cudaMemcpy(&v, c->d_guard, sizeof(v), cudaMemcpyDeviceToHost));
     *count = (long)v;
     return LBM_OK;
+}
+
+lbm_status lbm_bounded_wait_selftest(lbm_ctx *c, double *waited_s)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    // the kernel writes the time it waited into the last slot of the result scratch
+    unsigned long long *d_ns = reinterpret_cast<unsigned long long *>(c->d_result + 7);
+    unsigned long long ns = 0;
+    cudaError_t e = launch_bounded_wait_selftest(c->d_err, d_ns, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+    if (waited_s) *waited_s = (double)ns * 1e-9;
+    return check_device_error(c);
 }
 
 // Checkpoint layout: 8-byte magic, then int32 {version, nx, ny, storage, gi_mode},

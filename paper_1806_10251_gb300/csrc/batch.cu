@@ -527,8 +527,10 @@ lbm_status tick(lbm_batch *b, bool *busy)
     if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, std::string("batch tick: ") + cudaGetErrorString(e));
     cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (err) {
-        cudaMemset(b->d_err, 0, sizeof(int));
-        cudaMemset(b->d_work, 0, 2 * sizeof(unsigned int));
+        // on the batch stream: later launches there see the cleared counters
+        cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+        cudaMemsetAsync(b->d_work, 0, 2 * sizeof(unsigned int), b->stream);
+        cudaStreamSynchronize(b->stream);
         return bfail(LBM_ERR_CUDA, "a batched step kernel's bounded wait expired");
     }
     const double t = seconds(b);

@@ -210,6 +210,7 @@ cudaError_t launch_residual(const StepParams &p, int storage, const void *f, dou
                             double *snap_uy, double *partials, int nblocks, double *result,
                             cudaStream_t s);
 int residual_blocks(const StepParams &p);
+cudaError_t launch_bounded_wait_selftest(int *error, unsigned long long *waited_ns, cudaStream_t s);
 cudaError_t launch_convert(const StepParams &p, int from_storage, const void *fin, int to_storage,
                            void *fout, cudaStream_t s);
 cudaError_t launch_pops_to_f64(const StepParams &p, int storage, const void *f, double *out,

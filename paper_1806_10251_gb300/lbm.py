@@ -101,6 +101,7 @@ SIGNATURES = {
     "lbm_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lbm_destroy": (None, [_P]),
     "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_bounded_wait_selftest": (ctypes.c_int, [_P, _DP]),
     "lbm_set_allocator": (ctypes.c_int, [ctypes.POINTER(Allocator)]),
     "lbm_kernel_launches": (ctypes.c_int, [_P, ctypes.POINTER(_L)]),
     "lbm_residual_sums_noalloc": (ctypes.c_int, [ctypes.POINTER(PopulationDesc), _P, _P, _P, _P, _P]),
@@ -313,6 +314,13 @@ class Solver:
         v = ctypes.c_long()
         check(lib().lbm_guard_count(self._h, ctypes.byref(v)))
         return v.value
+
+    def bounded_wait_selftest(self):
+        """Run lbm_bounded_wait_selftest; returns (status, seconds waited) without
+        raising (the expected status is ERR_CUDA)."""
+        w = ctypes.c_double()
+        st = lib().lbm_bounded_wait_selftest(self._h, ctypes.byref(w))
+        return st, w.value
 
     def save(self, path: str):
         check(lib().lbm_save(self._h, os.fspath(path).encode()))
