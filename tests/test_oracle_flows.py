@@ -1,7 +1,8 @@
 """Whole-domain pins of the FP64 oracle: conservation, fixed points and flows
 whose answer is known in closed form (Couette, Poiseuille, shear-wave and
 Taylor-Green decay rates), the Galilean-invariance test in a moving frame, and
-the four-rolls mill against its analytic solution."""
+the four-rolls mill against the steady solution of the preconditioned
+Navier-Stokes system (continuum_ns) and its incompressible limit."""
 import json
 import os
 
@@ -10,6 +11,7 @@ import pytest
 
 import oracle as orc
 import workloads as wl
+from continuum_ns import PeriodicSteadyNS
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -191,22 +193,80 @@ def test_steady_cavity_independent_of_gamma_under_refinement():
     assert diffs[1] < 0.4 * diffs[0], diffs
 
 
-def test_four_rolls_mill_against_analytic():
-    """Variable body force F = 2 nu u0 (sin x sin y, cos x cos y) (Sec. 6.5): the
-    steady field must approach u0 (sin x sin y, cos x cos y).  Table I's values
-    depend on relaxation rates the paper does not give; only their magnitude is
-    checked here (global relative error below 1e-2 for both kernels)."""
+def _four_rolls_continuum(n, u0, gamma, Re=20.0, M=15):
+    """Steady four-rolls field of the preconditioned NS system (continuum_ns) on
+    the n x n lattice nodes, with the force of the workload recipe."""
+    c = wl.four_rolls_mill(n, u0, Re, gamma)
+    P = PeriodicSteadyNS(n, M, c.nu, gamma)
+    k = 2 * np.pi / n
+    sx, sy, cx, cy = np.sin(k * P.X), np.sin(k * P.Y), np.cos(k * P.X), np.cos(k * P.Y)
+    F = 2 * c.nu * u0 * k * k
+    rho, ux, uy, res = P.solve(F * sx * sy, F * cx * cy, u0 * sx * sy, u0 * cx * cy)
+    assert res < 1e-10 * F, res
+    return c, P.to_lattice(ux), P.to_lattice(uy)
+
+
+def _gre(a, b):
+    """Global relative error of Sec. 6.5: sqrt(sum (a - b)^2 / sum b^2)."""
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def _four_rolls_oracle(c, gi_mode, chunk=500, tol=1e-11, max_steps=40000):
+    d = make(c, gi_mode)
+    while d.steps < max_steps:
+        d.step(chunk)
+        r, _ = d.residual()
+        if r < tol:
+            break
+    assert r < tol
+    _, u, v = d.fields()
+    return u, v
+
+
+def test_four_rolls_mill_incompressible_field_is_the_low_mach_limit():
+    """The printed four-rolls field u0 (sin x sin y, cos x cos y) solves the
+    incompressible equations (Sec. 6.5).  The scheme solves the preconditioned
+    system (Eq. 1) with p* = gamma rho / 3, whose steady state carries a density
+    variation of order 3 u0^2 / gamma and departs from the printed field by a
+    relative amount proportional to u0^2 / gamma, independent of the grid and
+    of the bulk rate omega3.  At Table I's u0 = 0.045 that departure
+    (1.6e-3 / gamma) exceeds every corrected error Table I prints, so the
+    printed field cannot be the reference the corrected errors are measured
+    against without this floor."""
     table = json.load(open(os.path.join(GOLDEN, "table1_four_rolls_mill.json")))
-    assert table["rows"][1]["gamma"] == 0.3
-    for gi_mode in (orc.GI_UNCORRECTED, orc.GI_FULL):
-        c = wl.four_rolls_mill(125, 0.045, 20.0, 0.5)
-        d = make(c, gi_mode)
-        d.step(2500)
-        _, u, v = d.fields()
-        ua, va = c.meta["ua"], c.meta["va"]
-        gu = np.sqrt(((u - ua) ** 2).sum() / (ua**2).sum())
-        gv = np.sqrt(((v - va) ** 2).sum() / (va**2).sum())
-        assert gu < 1e-2 and gv < 1e-2, (gi_mode, gu, gv)
+    floor = {}
+    for n, u0, g in ((63, 0.045, 0.3), (63, 0.0225, 0.3), (63, 0.045, 0.5), (125, 0.045, 0.3)):
+        c, uc, vc = _four_rolls_continuum(n, u0, g)
+        floor[(n, u0, g)] = _gre(uc, c.meta["ua"])
+        assert np.isclose(_gre(vc, c.meta["va"]), floor[(n, u0, g)], rtol=1e-6)
+    assert 3.9 < floor[(63, 0.045, 0.3)] / floor[(63, 0.0225, 0.3)] < 4.1        # u0^2
+    assert 1.6 < floor[(63, 0.045, 0.3)] / floor[(63, 0.045, 0.5)] < 1.75        # 1/gamma
+    assert abs(floor[(125, 0.045, 0.3)] / floor[(63, 0.045, 0.3)] - 1) < 1e-2   # grid-free
+    for row in table["rows"]:
+        if row["gamma"] in (0.3, 0.5):
+            assert floor[(63, 0.045, row["gamma"])] > 1.5 * row["corrected_u"]
+
+
+def test_four_rolls_mill_corrected_scheme_converges_to_the_preconditioned_ns_solution():
+    """Table I's claim, that the GI corrections remove the error the
+    uncorrected scheme makes in this forced flow with nonzero diagonal strain
+    rates, checked against the steady solution of the equations the corrected
+    scheme is derived to solve (Eqs. 42-49; continuum_ns, independent of any
+    lattice arithmetic) at Table I's u0 = 0.045, Re = 20, gamma = 0.3.  The
+    corrected scheme's error against it falls under refinement (63^2 -> 125^2)
+    and ends far below the uncorrected scheme's, which stays at its
+    grid-independent cubic-velocity level (Eqs. 26-28)."""
+    err = {}
+    for n in (63, 125):
+        c, uc, vc = _four_rolls_continuum(n, 0.045, 0.3)
+        for mode in (orc.GI_UNCORRECTED, orc.GI_FULL):
+            u, v = _four_rolls_oracle(c, mode)
+            err[(n, mode)] = max(_gre(u, uc), _gre(v, vc))
+    full63, full125 = err[(63, orc.GI_FULL)], err[(125, orc.GI_FULL)]
+    unc63, unc125 = err[(63, orc.GI_UNCORRECTED)], err[(125, orc.GI_UNCORRECTED)]
+    assert full125 < 5e-4 and full125 < 0.5 * full63, err
+    assert unc125 > 0.8 * unc63, err
+    assert unc125 > 10 * full125, err
 
 
 def _steady_profile(c, chunk=500, max_steps=100000):

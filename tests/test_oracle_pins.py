@@ -355,6 +355,44 @@ def test_source_moments_are_moments_of_source():
     assert np.isclose(np.dot(S, EX), 1e-3 / 0.4) and np.isclose(np.dot(S, EY), -2e-3 / 0.4)
 
 
+def test_source_moments_gamma1_are_the_shifted_first_order_source():
+    """At gamma = 1 the raw source moments listed after Eq. 15 are those of the
+    unpreconditioned cascaded forcing the paper builds on: a source whose
+    central moments about u are (0, F_x, F_y) at orders 0 and 1 and zero at
+    every higher order.  Computed here independently: the populations
+    S = T^-1 sigma' are shifted to central moments about u by direct
+    summation of (e - u)^m (e - u)^n, so a dropped factor or a wrong sign in
+    any of sigma'_xx ... sigma'_xxyy leaves a nonzero higher central moment."""
+    rng = np.random.default_rng(11)
+    for _ in range(30):
+        Fx, Fy = rng.uniform(-1e-3, 1e-3, 2)
+        ux, uy = rng.uniform(-0.15, 0.15, 2)
+        S = orc.pops_from_raw(orc.source_moments(Fx, Fy, ux, uy, 1.0))
+        c = _central_from_pops(S, ux, uy)
+        tol = 1e-14 * max(abs(Fx), abs(Fy))
+        assert abs(c[0]) < tol
+        assert abs(c[1] - Fx) < tol and abs(c[2] - Fy) < tol
+        assert np.abs(c[3:]).max() < tol, c
+
+
+def test_source_moments_gamma_scaling():
+    """The preconditioning of the source moments stated after Eq. 15: the F_i
+    terms (first order) carry 1/gamma, the F_i u_j terms (second order)
+    1/gamma^2, and the third- and fourth-order moments are printed without a
+    gamma.  Checked as ratios to the gamma = 1 moments, which the previous
+    test fixes, for the nine components one by one."""
+    rng = np.random.default_rng(12)
+    power = np.array([0, 1, 1, 2, 2, 2, 0, 0, 0])
+    for _ in range(30):
+        Fx, Fy = rng.uniform(-1e-3, 1e-3, 2)
+        ux, uy = rng.uniform(-0.15, 0.15, 2)
+        g = rng.uniform(0.1, 1.0)
+        s1 = orc.source_moments(Fx, Fy, ux, uy, 1.0)
+        sg = orc.source_moments(Fx, Fy, ux, uy, g)
+        assert sg[0] == 0.0 and s1[0] == 0.0
+        assert np.allclose(sg[1:] * g ** power[1:], s1[1:], rtol=1e-13, atol=1e-22)
+
+
 def _gradient(nx, ny, sides, fd, rho, solid=None):
     d = orc.Domain(nx, ny, 0.05, 0.5, sides, fd=fd, solid=solid)
     return d.density_gradient(rho)
