@@ -1,8 +1,10 @@
 """Compile the CUDA library in-tree for sm_103a (GB300).
 
 Each translation unit is compiled by nvcc in parallel, then linked into
-``paper_1806_10251_gb300/_build/liblbm_gb300.so``.  Rebuilds only when a source
-or header is newer than the library.
+``paper_1806_10251_gb300/_build/liblbm_gb300.so``.  ``variants.cu`` is compiled
+once per (storage type, group of kernel variants) with the defines of
+``VARIANT_MATRIX``, so that the large step and batch kernels compile on all
+cores at once.  Rebuilds only when a source or header is newer than the library.
 """
 from __future__ import annotations
 
@@ -20,6 +22,10 @@ LIB = os.path.join(BUILD, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE]
+
+
+# variants.cu: storage types 0..3 (LBM_STORAGE_*) x groups 0..3 of variants
+VARIANT_MATRIX = [(st, part) for st in range(4) for part in range(4)]
 
 
 def _nvcc() -> str:
@@ -48,12 +54,22 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    srcs = sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    jobs = []  # (source, object, defines)
+    for src in sources():
+        stem = os.path.basename(src)[:-3]
+        if stem == "variants":
+            for st, part in VARIANT_MATRIX:
+                jobs.append((src, os.path.join(BUILD, f"variants_s{st}_p{part}.o"),
+                             [f"-DLBM_VARIANT_STORAGE={st}", f"-DLBM_VARIANT_PART={part}"]))
+        else:
+            jobs.append((src, os.path.join(BUILD, stem + ".o"), []))
+    # the largest units first, so that the small ones fill in around them
+    jobs.sort(key=lambda j: os.path.basename(j[0]) != "variants.cu")
+    objs = [j[1] for j in jobs]
 
-    def compile_one(pair):
-        src, obj = pair
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+    def compile_one(job):
+        src, obj, defines = job
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defines, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0 or verbose:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
@@ -61,8 +77,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}")
         return r.stderr
 
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        list(ex.map(compile_one, zip(srcs, objs)))
+    with ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 1, len(jobs)))) as ex:
+        list(ex.map(compile_one, jobs))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     subprocess.run(cmd, check=True)

@@ -657,128 +657,4 @@ stream_collide_batch_kernel(const __grid_constant__ BatchArgs a)
     warp_end<ST>(w, abort, a.error, a.work);
 }
 
-template <typename ST, int MODE>
-cudaError_t launch_batch_mode(bool forced, const BatchArgs &a, int grid, cudaStream_t s)
-{
-    using T = Tile<ST>;
-    if (forced) stream_collide_batch_kernel<ST, MODE, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
-    else stream_collide_batch_kernel<ST, MODE, false><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename ST>
-cudaError_t launch_batch_t(int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s)
-{
-    switch (gi_mode) {
-    case LBM_GI_UNCORRECTED: return launch_batch_mode<ST, LBM_GI_UNCORRECTED>(forced, a, grid, s);
-    case LBM_GI_CUBIC_ONLY: return launch_batch_mode<ST, LBM_GI_CUBIC_ONLY>(forced, a, grid, s);
-    default: return launch_batch_mode<ST, LBM_GI_FULL>(forced, a, grid, s);
-    }
-}
-
-template <typename ST, int MODE, bool FORCED>
-int batch_blocks_variant()
-{
-    using T = Tile<ST>;
-    auto fn = stream_collide_batch_kernel<ST, MODE, FORCED>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM_BYTES) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, THREADS, T::SMEM_BYTES) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    return n > 0 ? n : 1;
-}
-
-template <typename ST>
-int batch_blocks_t(int gi_mode, bool forced)
-{
-    switch (gi_mode) {
-    case LBM_GI_UNCORRECTED:
-        return forced ? batch_blocks_variant<ST, LBM_GI_UNCORRECTED, true>()
-                      : batch_blocks_variant<ST, LBM_GI_UNCORRECTED, false>();
-    case LBM_GI_CUBIC_ONLY:
-        return forced ? batch_blocks_variant<ST, LBM_GI_CUBIC_ONLY, true>()
-                      : batch_blocks_variant<ST, LBM_GI_CUBIC_ONLY, false>();
-    default:
-        return forced ? batch_blocks_variant<ST, LBM_GI_FULL, true>() : batch_blocks_variant<ST, LBM_GI_FULL, false>();
-    }
-}
-
-template <typename ST>
-cudaError_t launch_step_t(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin,
-                          int grid, cudaStream_t s)
-{
-    using T = Tile<ST>;
-    const ST *in = static_cast<const ST *>(fin);
-    const bool forced = p.force != nullptr || p.Fx != 0.0 || p.Fy != 0.0;
-#define LBM_LAUNCH(M, F) stream_collide_kernel<ST, M, F><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, tout, in)
-    if (p.fd_iso && p.gi_mode == LBM_GI_FULL) {
-        // the density gradient enters the full kernel only
-        if (forced) stream_collide_kernel<ST, LBM_GI_FULL, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, tout, in);
-        else stream_collide_kernel<ST, LBM_GI_FULL, false, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, tout, in);
-        return cudaGetLastError();
-    }
-    switch (p.gi_mode) {
-    case LBM_GI_UNCORRECTED:
-        if (forced) LBM_LAUNCH(LBM_GI_UNCORRECTED, true);
-        else LBM_LAUNCH(LBM_GI_UNCORRECTED, false);
-        break;
-    case LBM_GI_CUBIC_ONLY:
-        if (forced) LBM_LAUNCH(LBM_GI_CUBIC_ONLY, true);
-        else LBM_LAUNCH(LBM_GI_CUBIC_ONLY, false);
-        break;
-    default:
-        if (forced) LBM_LAUNCH(LBM_GI_FULL, true);
-        else LBM_LAUNCH(LBM_GI_FULL, false);
-        break;
-    }
-#undef LBM_LAUNCH
-    return cudaGetLastError();
-}
-
-template <typename ST, int MODE, bool FORCED, bool ISO = false>
-int blocks_per_sm_variant()
-{
-    using T = Tile<ST>;
-    auto fn = stream_collide_kernel<ST, MODE, FORCED, ISO>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM_BYTES) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, THREADS, T::SMEM_BYTES) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    return n > 0 ? n : 1;
-}
-
-// Resident blocks per SM of the variant a launch with these settings uses (its
-// dynamic shared-memory attribute is set on the way).
-template <typename ST, int MODE>
-int blocks_per_sm_mode(bool forced)
-{
-    return forced ? blocks_per_sm_variant<ST, MODE, true>() : blocks_per_sm_variant<ST, MODE, false>();
-}
-
-template <typename ST>
-int blocks_per_sm_t(int gi_mode, bool forced)
-{
-    switch (gi_mode) {
-    case LBM_GI_UNCORRECTED: return blocks_per_sm_mode<ST, LBM_GI_UNCORRECTED>(forced);
-    case LBM_GI_CUBIC_ONLY: return blocks_per_sm_mode<ST, LBM_GI_CUBIC_ONLY>(forced);
-    default: {
-        // the isotropic-gradient variant gets its shared-memory attribute too
-        const int a = blocks_per_sm_mode<ST, LBM_GI_FULL>(forced);
-        const int i = forced ? blocks_per_sm_variant<ST, LBM_GI_FULL, true, true>()
-                             : blocks_per_sm_variant<ST, LBM_GI_FULL, false, true>();
-        return a < i ? a : i;
-    }
-    }
-}
-
 }  // namespace lbm

@@ -655,45 +655,6 @@ stream_collide_x2_batch_kernel(const __grid_constant__ BatchArgs a)
     warp_end_x2<ST>(w, abort, a.error, a.work);
 }
 
-template <typename ST>
-cudaError_t launch_step_x2_t(const StepParams &p, const CUtensorMap &tin, const void *fin, void *fout, int grid,
-                             cudaStream_t s)
-{
-    using T = Tile2<ST>;
-    const ST *in = static_cast<const ST *>(fin);
-    ST *out = static_cast<ST *>(fout);
-    const bool forced = p.force != nullptr || p.Fx != 0.0 || p.Fy != 0.0;
-#define LBM_LAUNCH(M, F) stream_collide_x2_kernel<ST, M, F><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out)
-    if (p.fd_iso && p.gi_mode == LBM_GI_FULL) {
-        // the density gradient enters the full kernel only
-        if (forced) stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
-        else stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
-        return cudaGetLastError();
-    }
-    if (p.guard && p.gi_mode == LBM_GI_FULL) {
-        // the guard acts in the full kernel only (the strain solve)
-        if (forced) stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
-        else stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(p, tin, in, out);
-        return cudaGetLastError();
-    }
-    switch (p.gi_mode) {
-    case LBM_GI_UNCORRECTED:
-        if (forced) LBM_LAUNCH(LBM_GI_UNCORRECTED, true);
-        else LBM_LAUNCH(LBM_GI_UNCORRECTED, false);
-        break;
-    case LBM_GI_CUBIC_ONLY:
-        if (forced) LBM_LAUNCH(LBM_GI_CUBIC_ONLY, true);
-        else LBM_LAUNCH(LBM_GI_CUBIC_ONLY, false);
-        break;
-    default:
-        if (forced) LBM_LAUNCH(LBM_GI_FULL, true);
-        else LBM_LAUNCH(LBM_GI_FULL, false);
-        break;
-    }
-#undef LBM_LAUNCH
-    return cudaGetLastError();
-}
-
 template <typename KernelFn>
 int occupancy_of(KernelFn fn, int smem)
 {
@@ -707,71 +668,6 @@ int occupancy_of(KernelFn fn, int smem)
         return 1;
     }
     return n > 0 ? n : 1;
-}
-
-// Resident blocks per SM of the step-kernel variant a launch with these
-// settings uses (its dynamic shared-memory attribute is set on the way).
-template <typename ST>
-int blocks_per_sm_x2_t(int gi_mode, bool forced)
-{
-    using T = Tile2<ST>;
-    switch (gi_mode) {
-    case LBM_GI_UNCORRECTED:
-        return forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_UNCORRECTED, true>, T::SMEM_BYTES)
-                      : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_UNCORRECTED, false>, T::SMEM_BYTES);
-    case LBM_GI_CUBIC_ONLY:
-        return forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, true>, T::SMEM_BYTES)
-                      : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_CUBIC_ONLY, false>, T::SMEM_BYTES);
-    default: {
-        // the guard and isotropic-gradient variants get their shared-memory
-        // attribute too (min of all three)
-        const int a = forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true>, T::SMEM_BYTES)
-                             : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false>, T::SMEM_BYTES);
-        const int b = forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true>, T::SMEM_BYTES)
-                             : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true>, T::SMEM_BYTES);
-        const int i = forced ? occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, true, true, true>, T::SMEM_BYTES)
-                             : occupancy_of(stream_collide_x2_kernel<ST, LBM_GI_FULL, false, true, true>, T::SMEM_BYTES);
-        const int ab = a < b ? a : b;
-        return ab < i ? ab : i;
-    }
-    }
-}
-
-template <typename ST, int MODE>
-cudaError_t launch_batch_x2_mode(bool forced, const BatchArgs &a, int grid, cudaStream_t s)
-{
-    using T = Tile2<ST>;
-    if (forced) stream_collide_x2_batch_kernel<ST, MODE, true><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
-    else stream_collide_x2_batch_kernel<ST, MODE, false><<<grid, THREADS, T::SMEM_BYTES, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename ST>
-cudaError_t launch_batch_x2_t(int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s)
-{
-    switch (gi_mode) {
-    case LBM_GI_UNCORRECTED: return launch_batch_x2_mode<ST, LBM_GI_UNCORRECTED>(forced, a, grid, s);
-    case LBM_GI_CUBIC_ONLY: return launch_batch_x2_mode<ST, LBM_GI_CUBIC_ONLY>(forced, a, grid, s);
-    default: return launch_batch_x2_mode<ST, LBM_GI_FULL>(forced, a, grid, s);
-    }
-}
-
-template <typename ST, int MODE>
-int batch_blocks_x2_mode(bool forced)
-{
-    using T = Tile2<ST>;
-    return forced ? occupancy_of(stream_collide_x2_batch_kernel<ST, MODE, true>, T::SMEM_BYTES)
-                  : occupancy_of(stream_collide_x2_batch_kernel<ST, MODE, false>, T::SMEM_BYTES);
-}
-
-template <typename ST>
-int batch_blocks_x2_t(int gi_mode, bool forced)
-{
-    switch (gi_mode) {
-    case LBM_GI_UNCORRECTED: return batch_blocks_x2_mode<ST, LBM_GI_UNCORRECTED>(forced);
-    case LBM_GI_CUBIC_ONLY: return batch_blocks_x2_mode<ST, LBM_GI_CUBIC_ONLY>(forced);
-    default: return batch_blocks_x2_mode<ST, LBM_GI_FULL>(forced);
-    }
 }
 
 }  // namespace lbm
