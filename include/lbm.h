@@ -258,10 +258,12 @@ void lbm_batch_destroy(lbm_batch *b);
  * queued on `stream` (a cudaStream_t; NULL = the default stream) and nothing
  * is allocated, freed or synchronised.
  *
- * The first call on a device looks up the scratch array's device address for
- * that device; make it before any stream capture.  All calls share the one
- * array: calls that overlap on the GPU race, so order them (e.g. one stream).
- * nx*ny above LBM_NOALLOC_MAX_CELLS gives LBM_ERR_INVALID. */
+ * The first call on a device (and the first after a cudaDeviceReset of it)
+ * looks up the scratch array's device address in the current context; make
+ * that call before any stream capture.  First calls from several host threads
+ * at once are safe.  All calls share the one array: calls that overlap on the
+ * GPU race, so order them (e.g. one stream).  nx*ny above
+ * LBM_NOALLOC_MAX_CELLS gives LBM_ERR_INVALID. */
 #define LBM_NOALLOC_MAX_PARTIALS 65536
 #define LBM_NOALLOC_MAX_CELLS (65536LL * 256LL)
 typedef struct {

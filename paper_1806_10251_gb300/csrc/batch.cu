@@ -82,6 +82,7 @@ struct Pending {
 
 struct Record {
     int slot = -1;
+    int readers = 0;  // lbm_batch_fields calls reading the slot's buffers; release waits for 0
     int state = LBM_REQ_QUEUED;
     long steps = 0;
     double residual = INFINITY;
@@ -736,21 +737,32 @@ lbm_status lbm_batch_fields(lbm_batch *b, long id, double *rho, double *ux, doub
             return bfail(LBM_ERR_INVALID, "request not finished (or released)");
         s = b->slots[it->second.slot];
         parity = b->parity;
+        // pin the slot: a concurrent lbm_batch_release waits until the read ends
+        ++it->second.readers;
     }
     const size_t N = (size_t)s.nx * s.ny;
     double *d = nullptr;
-    if (cudaMalloc((void **)&d, 3 * N * sizeof(double)) != cudaSuccess) {
+    cudaError_t e = cudaMalloc((void **)&d, 3 * N * sizeof(double));
+    lbm_status st = LBM_OK;
+    if (e != cudaSuccess) {
         cudaGetLastError();
-        return bfail(LBM_ERR_OOM, "device allocation failed (fields)");
+        st = bfail(LBM_ERR_OOM, "device allocation failed (fields)");
+    } else {
+        e = launch_fields(s.p, b->storage, s.f[parity], d, d + N, d + 2 * N, b->io_stream);
+        if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, d, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
+        if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, d + N, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
+        if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->io_stream);
+        cudaFree(d);
+        if (e != cudaSuccess) st = bfail(LBM_ERR_CUDA, std::string("batch fields: ") + cudaGetErrorString(e));
     }
-    cudaError_t e = launch_fields(s.p, b->storage, s.f[parity], d, d + N, d + 2 * N, b->io_stream);
-    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, d, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
-    if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, d + N, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
-    if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->io_stream);
-    cudaFree(d);
-    if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, std::string("batch fields: ") + cudaGetErrorString(e));
-    return LBM_OK;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        auto it = b->records.find(id);
+        if (it != b->records.end()) --it->second.readers;
+    }
+    b->cv.notify_all();
+    return st;
 }
 
 lbm_status lbm_batch_release(lbm_batch *b, long id)
@@ -758,10 +770,17 @@ lbm_status lbm_batch_release(lbm_batch *b, long id)
     if (!b) return bfail(LBM_ERR_INVALID, "null batch");
     Slot s;
     {
-        std::lock_guard<std::mutex> lk(b->mu);
+        std::unique_lock<std::mutex> lk(b->mu);
         auto it = b->records.find(id);
         if (it == b->records.end()) return bfail(LBM_ERR_INVALID, "unknown request id");
         if (it->second.state < LBM_REQ_CONVERGED) return bfail(LBM_ERR_INVALID, "request not finished");
+        // buffers being read by lbm_batch_fields stay until those reads end
+        b->cv.wait(lk, [&] {
+            auto jt = b->records.find(id);
+            return jt == b->records.end() || jt->second.readers == 0;
+        });
+        it = b->records.find(id);
+        if (it == b->records.end()) return bfail(LBM_ERR_INVALID, "unknown request id");
         const int si = it->second.slot;
         if (si >= 0) {
             s = b->slots[si];

@@ -261,3 +261,37 @@ def test_batch_option_and_request_validation():
     with pytest.raises(lbm.LbmError):
         b.poll(12345)
     b.close()
+
+
+def test_fields_and_release_from_two_threads():
+    """lbm_batch_fields and lbm_batch_release on the same finished request from
+    two host threads: every fields call either returns the full result or is
+    refused because the request was released; release waits for reads in
+    flight, so no read sees freed memory (ctypes drops the GIL in each call)."""
+    import threading
+
+    c = wl.cavity(256, 100.0, 0.1, 0.5)
+    for trial in range(3):
+        b = lbm.Batch(1 << 28, storage=lbm.STORAGE_F32)
+        b.set_option("check_every", 100)
+        rid = b.submit_case(c, tol=1e-300, max_steps=200)
+        b.run()
+        ref = b.fields(rid, c.nx, c.ny)
+        outcomes = []
+
+        def reader():
+            for _ in range(40):
+                try:
+                    got = b.fields(rid, c.nx, c.ny)
+                    outcomes.append(all(np.array_equal(g, r, equal_nan=True) for g, r in zip(got, ref)))
+                except lbm.LbmError as e:
+                    outcomes.append(e.status == lbm.ERR_INVALID and "released" in str(e) or
+                                    e.status == lbm.ERR_INVALID and "unknown" in str(e))
+
+        t = threading.Thread(target=reader)
+        t.start()
+        time.sleep(0.001 * trial)
+        b.release(rid)
+        t.join()
+        assert outcomes and all(outcomes), outcomes
+        b.close()

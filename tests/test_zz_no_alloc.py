@@ -53,6 +53,48 @@ def test_noalloc_sums_match_lbm_residual_on_two_calls():
         assert np.allclose(snap_v.cpu().numpy(), v, rtol=0, atol=1e-15)
 
 
+def test_noalloc_pitched_fp16_with_solid_and_force():
+    """The descriptor's other paths: a plane pitch above nx (200 cells in rows of
+    256), a solid mask on the device, a uniform body force (rho u = sum f e -
+    F/(2 gamma)) and FP16 storage (2^14 (f - w) as half).  The populations are
+    the context's own, re-encoded from its host copy; the sums must equal
+    lbm_residual's on that context on two calls in a row."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    case = wl.random_cavity_state(200, 90, 0.5, Re=60.0, seed=13)
+    case.Fx, case.Fy = 2e-6, -1e-6
+    solid = np.zeros((case.ny, case.nx), np.uint8)
+    solid[30:52, 80:111] = 1
+    case.solid = solid
+    ref = lbm.solver_from_case(case, storage=lbm.STORAGE_F16)
+    pitch = 256
+    _, u0, v0 = ref.fields()
+    snap_u = torch.from_numpy(np.nan_to_num(u0)).cuda()
+    snap_v = torch.from_numpy(np.nan_to_num(v0)).cuda()
+    mask = np.zeros((case.ny, pitch), np.uint8)
+    mask[:, :case.nx] = solid
+    mask_dev = torch.from_numpy(mask).cuda()
+    sums = torch.zeros(5, dtype=torch.float64, device="cuda")
+    desc = lbm.PopulationDesc(case.nx, case.ny, pitch, lbm.STORAGE_F16, case.gamma, case.Fx, case.Fy,
+                              mask_dev.data_ptr())
+    for steps in (30, 17):
+        ref.step(steps)
+        _, expected = ref.residual()
+        f = ref.populations()
+        g = np.zeros((9, case.ny, pitch), np.float16)
+        g[:, :, :case.nx] = (16384.0 * (f - W[:, None, None])).astype(np.float16)
+        # the re-encoding reproduces the host copy to rounding (the stored half values)
+        back = g[:, :, :case.nx].astype(np.float64) / 16384.0 + W[:, None, None]
+        assert np.abs(back - f).max() < 1e-15
+        f_dev = torch.from_numpy(g.view(np.int16)).cuda()
+        lbm.residual_sums_noalloc(desc, f_dev.data_ptr(), snap_u.data_ptr(), snap_v.data_ptr(), sums.data_ptr())
+        torch.cuda.synchronize()
+        got = sums.cpu().numpy()
+        assert np.allclose(got, expected, rtol=1e-12, atol=1e-12), (got, expected)
+        assert got[2] < case.cells - solid.sum() + 1.0  # solid cells are left out of sum rho
+
+
 def test_noalloc_rejects_domains_beyond_the_scratch():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
