@@ -28,7 +28,7 @@ _lib = None
 
 GI_UNCORRECTED, GI_CUBIC_ONLY, GI_FULL = 0, 1, 2
 FD_CENTRAL, FD_ISOTROPIC = 0, 1
-SIDE_PERIODIC, SIDE_WALL, SIDE_MOVING_WALL = 0, 1, 2
+SIDE_PERIODIC, SIDE_WALL, SIDE_MOVING_WALL, SIDE_INLET, SIDE_OUTLET = 0, 1, 2, 3, 4
 
 
 class OrcParams(ctypes.Structure):
@@ -81,6 +81,7 @@ def lib():
             L.orc_steps_done.argtypes = [ctypes.c_void_p]
             L.orc_guard_count.restype = ctypes.c_long
             L.orc_guard_count.argtypes = [ctypes.c_void_p]
+            L.orc_drag.argtypes = [ctypes.c_void_p, dp]
             L.orc_density_gradient_field.argtypes = [ctypes.c_void_p] * 4
             L.orc_set_threads.argtypes = [ctypes.c_int]
             L.orc_get_threads.restype = ctypes.c_int
@@ -215,6 +216,12 @@ class Domain:
         s = np.zeros(5)
         r = lib().orc_residual(self._h, _dp(s))
         return r, s
+
+    def drag(self):
+        """Momentum-exchange force on the solid cells (lattice momentum per step)."""
+        F = np.zeros(2)
+        lib().orc_drag(self._h, _dp(F))
+        return F
 
 
 def set_threads(n: int) -> None:

@@ -33,6 +33,21 @@
  *     (a corner) sees a stationary wall;
  *   - density gradient: central difference on the same step's post-streaming
  *     rho; a missing neighbour (wall side or solid) takes the cell's own rho;
+ *   - open boundaries of the square-cylinder channel (Sec. 6 gives the inlet
+ *     profile and the outlet equation only): the parabolic inlet is imposed
+ *     by half-way bounce-back with the moving-wall term (rho0 = 1), the wall
+ *     velocity taken at the point where the link crosses the inlet plane; the
+ *     convective outlet equation d_t u + U d_x u = 0 advances the velocity u_g
+ *     of a ghost column at x = nx, explicitly and upwind with unit lattice
+ *     steps (u_g <- u_g + U (u(nx-1) - u_g) after every collision), and the
+ *     populations that enter through the east side (e_x = -1) are the
+ *     equilibrium (Eq. 15) at the reference density rho0 = 1 and u_g plus the
+ *     non-equilibrium part f~ - f_eq of the last column (the reference density
+ *     fixes the pressure level, which a velocity condition leaves free); u_g
+ *     starts from the initial velocity of the last column; a link crossing two
+ *     sides (a corner) sees a stationary wall;
+ *   - momentum-exchange force: 2 e_a f~_a(x) summed over the links from fluid
+ *     cells x to solid cells x + e_a (half-way bounce-back, stationary solid);
  *   - strain-rate guard (optional, off by default): if |D| < 0.1 |D0| the
  *     velocity-dependent parts P, Q, P~, Q~ are dropped for that cell.
  *     Parity unpinned against the paper (it is silent on the case); the
@@ -312,6 +327,7 @@ struct orc_domain {
     double *uxs, *uys;          /* velocity snapshot for the residual */
     double *Fx, *Fy;            /* optional force field               */
     uint8_t *solid;
+    double *ghost;              /* convective outlet at x = nx, [5][ny]: u_g, v_g and f~ of 3, 6, 7 */
     long steps;
     long guard_count;
 };
@@ -334,6 +350,62 @@ static int is_solid(const orc_domain *d, int x, int y)
     return d->solid ? d->solid[(long)y * d->p.nx + x] != 0 : 0;
 }
 
+/* ghost-column index of the directions with e_x = -1 (3, 6, 7); -1 otherwise */
+static int ghost_index(int a) { return a == 3 ? 0 : (a == 6 ? 1 : (a == 7 ? 2 : -1)); }
+
+/* Parabolic inlet profile (Sec. 6): u(y) = 4 U_max (y + 1/2)(H - y - 1/2) / H^2
+ * between the walls at y = -1/2 and H - 1/2, H = ny. */
+static double inlet_velocity(const orc_params *p, double y)
+{
+    const double H = p->ny, t = y + 0.5;
+    return 4.0 * p->side_u[ORC_WEST][0] * t * (H - t) / (H * H);
+}
+
+/* Populations f_eq of the preconditioned equilibrium (Eq. 15, through the
+ * inverse of Eq. 5). */
+static void equilibrium_pops(double rho, double ux, double uy, double g, double feq[9])
+{
+    double keq[9];
+    orc_raw_equilibrium(rho, ux, uy, g, keq);
+    orc_pops_from_raw(keq, feq);
+}
+
+/* Velocity of a cell of the stored state (moments of f~ with the forcing
+ * shift, as orc_fields). */
+static void cell_velocity(const orc_domain *d, long i, double *rho, double *ux, double *uy);
+
+/* Convective outlet, one ghost row: given its velocity u_g, the incoming
+ * populations are f_eq(rho0, u_g) + (f~ - f_eq(rho, u)) of the last column. */
+static void outlet_populations(orc_domain *d, int y)
+{
+    const int nx = d->p.nx, ny = d->p.ny;
+    const long i = (long)y * nx + nx - 1;
+    double rho, ux, uy, fe[9], fg[9];
+    cell_velocity(d, i, &rho, &ux, &uy);
+    equilibrium_pops(rho, ux, uy, d->p.gamma, fe);
+    equilibrium_pops(d->p.rho0, d->ghost[y], d->ghost[ny + y], d->p.gamma, fg);
+    for (int a = 3; a <= 7; ++a) {
+        const int gi = ghost_index(a);
+        if (gi < 0) continue;
+        d->ghost[(2 + gi) * ny + y] = fg[a] + (d->f[a * d->N + i] - fe[a]);
+    }
+}
+
+/* ghost velocity <- the last column's velocity, then the incoming populations */
+static void outlet_seed(orc_domain *d)
+{
+    if (!d->ghost) return;
+    const int nx = d->p.nx, ny = d->p.ny;
+    for (int y = 0; y < ny; ++y) {
+        const long i = (long)y * nx + nx - 1;
+        double rho, ux, uy;
+        cell_velocity(d, i, &rho, &ux, &uy);
+        d->ghost[y] = ux;
+        d->ghost[ny + y] = uy;
+        outlet_populations(d, y);
+    }
+}
+
 orc_domain *orc_create(const orc_params *p, const uint8_t *solid)
 {
     if (p->nx < 3 || p->ny < 3) return NULL;
@@ -352,14 +424,17 @@ orc_domain *orc_create(const orc_params *p, const uint8_t *solid)
         d->solid = (uint8_t *)malloc(d->N);
         if (d->solid) memcpy(d->solid, solid, d->N);
     }
+    const int outlet = p->side_kind[ORC_EAST] == ORC_SIDE_OUTLET;
+    if (outlet) d->ghost = (double *)calloc(5 * (size_t)p->ny, sizeof(double));
     if (!d->f || !d->fbar || !d->rho || !d->ux || !d->uy || !d->uxs || !d->uys ||
-        (solid && !d->solid)) {
+        (solid && !d->solid) || (outlet && !d->ghost)) {
         orc_destroy(d);
         return NULL;
     }
     /* rest state */
     for (int a = 0; a < 9; ++a)
         for (long i = 0; i < d->N; ++i) d->f[a * d->N + i] = W[a];
+    outlet_seed(d);
     return d;
 }
 
@@ -367,7 +442,7 @@ void orc_destroy(orc_domain *d)
 {
     if (!d) return;
     free(d->f); free(d->fbar); free(d->rho); free(d->ux); free(d->uy);
-    free(d->uxs); free(d->uys); free(d->Fx); free(d->Fy); free(d->solid);
+    free(d->uxs); free(d->uys); free(d->Fx); free(d->Fy); free(d->solid); free(d->ghost);
     free(d);
 }
 
@@ -395,12 +470,14 @@ void orc_init_equilibrium(orc_domain *d, const double *rho, const double *ux, co
         orc_pops_from_raw(s, S);
         for (int a = 0; a < 9; ++a) d->f[a * d->N + i] = feq[a] - 0.5 * S[a];
     }
+    outlet_seed(d);
     d->steps = 0;
     double sums[5];
     orc_residual(d, sums); /* snapshot of the initial velocity */
 }
 
-/* Eq. 2b in pull form with half-way bounce-back (momentum-augmented). */
+/* Eq. 2b in pull form with half-way bounce-back (momentum-augmented); the
+ * open sides of the square-cylinder channel as in the readings above. */
 static void stream_cell(orc_domain *d, int x, int y, double fb[9])
 {
     const orc_params *p = &d->p;
@@ -424,6 +501,11 @@ static void stream_cell(orc_domain *d, int x, int y, double fb[9])
             if (p->side_kind[side] == ORC_SIDE_MOVING_WALL) {
                 uw = p->side_u[side][0];
                 vw = p->side_u[side][1];
+            } else if (p->side_kind[side] == ORC_SIDE_INLET) {
+                uw = inlet_velocity(p, 0.5 * (sy + y));  /* where the link crosses x = -1/2 */
+            } else if (p->side_kind[side] == ORC_SIDE_OUTLET) {
+                fb[a] = d->ghost[(2 + ghost_index(a)) * ny + sy];
+                continue;
             }
         }
         fb[a] = d->f[OPP[a] * N + i] + 6.0 * W[a] * p->rho0 * (EX[a] * uw + EY[a] * vw);
@@ -517,14 +599,71 @@ void orc_step(orc_domain *d, long n)
                 for (int a = 0; a < 9; ++a) d->f[a * N + i] = ft[a];
             }
         d->guard_count += guards;
+        /* convective outlet: advance the ghost velocity with the new last column */
+        if (d->ghost) {
+            const double U = d->p.side_u[ORC_EAST][0];
+            for (int y = 0; y < ny; ++y) {
+                if (is_solid(d, nx - 1, y)) continue;
+                double rho, ux, uy;
+                cell_velocity(d, (long)y * nx + nx - 1, &rho, &ux, &uy);
+                d->ghost[y] += U * (ux - d->ghost[y]);
+                d->ghost[ny + y] += U * (uy - d->ghost[ny + y]);
+                outlet_populations(d, y);
+            }
+        }
         d->steps += 1;
     }
 }
 
 void orc_get_pops(const orc_domain *d, double *f) { memcpy(f, d->f, 9 * d->N * sizeof(double)); }
-void orc_set_pops(orc_domain *d, const double *f) { memcpy(d->f, f, 9 * d->N * sizeof(double)); }
+void orc_set_pops(orc_domain *d, const double *f)
+{
+    memcpy(d->f, f, 9 * d->N * sizeof(double));
+    outlet_seed(d);
+}
 long orc_steps_done(const orc_domain *d) { return d->steps; }
 long orc_guard_count(const orc_domain *d) { return d->guard_count; }
+
+/* Momentum exchange (Sec. 6, square cylinder): the population f~_a(x) of a
+ * fluid cell that heads into a solid cell x + e_a returns as f~_a(x) in the
+ * opposite direction at the next streaming, handing the solid 2 e_a f~_a(x). */
+void orc_drag(const orc_domain *d, double force[2])
+{
+    const orc_params *p = &d->p;
+    const int nx = p->nx, ny = p->ny;
+    const int perx = p->side_kind[ORC_WEST] == ORC_SIDE_PERIODIC;
+    const int pery = p->side_kind[ORC_SOUTH] == ORC_SIDE_PERIODIC;
+    double fx = 0.0, fy = 0.0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (is_solid(d, x, y)) continue;
+            for (int a = 1; a < 9; ++a) {
+                int tx = x + EX[a], ty = y + EY[a];
+                if (perx) tx = (tx + nx) % nx;
+                if (pery) ty = (ty + ny) % ny;
+                if (tx < 0 || tx >= nx || ty < 0 || ty >= ny || !is_solid(d, tx, ty)) continue;
+                const double fa = d->f[a * d->N + (long)y * nx + x];
+                fx += 2.0 * EX[a] * fa;
+                fy += 2.0 * EY[a] * fa;
+            }
+        }
+    force[0] = fx;
+    force[1] = fy;
+}
+
+static void cell_velocity(const orc_domain *d, long i, double *rho, double *ux, double *uy)
+{
+    double r = 0.0, jx = 0.0, jy = 0.0;
+    for (int a = 0; a < 9; ++a) {
+        const double fa = d->f[a * d->N + i];
+        r += fa;
+        jx += fa * EX[a];
+        jy += fa * EY[a];
+    }
+    *rho = r;
+    *ux = (jx - 0.5 * force_x(d, i) / d->p.gamma) / r;
+    *uy = (jy - 0.5 * force_y(d, i) / d->p.gamma) / r;
+}
 
 /* Observed fields: local moments of the stored post-collision array, with the
  * forcing shift, rho u = sum f~ e - F/(2 gamma).  Because the collision

@@ -32,7 +32,13 @@ extern "C" {
 
 enum { ORC_GI_UNCORRECTED = 0, ORC_GI_CUBIC_ONLY = 1, ORC_GI_FULL = 2 };
 enum { ORC_FD_CENTRAL = 0, ORC_FD_ISOTROPIC = 1 };
-enum { ORC_SIDE_PERIODIC = 0, ORC_SIDE_WALL = 1, ORC_SIDE_MOVING_WALL = 2 };
+/* Side kinds.  INLET (west side only): fully developed parabolic velocity
+ * profile of peak side_u[WEST][0] across the channel, imposed by half-way
+ * bounce-back with the moving-wall term.  OUTLET (east side only): convective
+ * outflow d_t phi + U d_x phi = 0 with U = side_u[EAST][0] (Sec. 6, square
+ * cylinder). */
+enum { ORC_SIDE_PERIODIC = 0, ORC_SIDE_WALL = 1, ORC_SIDE_MOVING_WALL = 2, ORC_SIDE_INLET = 3,
+       ORC_SIDE_OUTLET = 4 };
 enum { ORC_WEST = 0, ORC_EAST = 1, ORC_SOUTH = 2, ORC_NORTH = 3 };
 
 typedef struct {
@@ -82,6 +88,9 @@ void   orc_used_fields(const orc_domain *d, double *rho, double *ux, double *uy)
 double orc_residual(orc_domain *d, double *sums /* 5: dU2, U2, mass, momx, momy */);
 long   orc_steps_done(const orc_domain *d);
 long   orc_guard_count(const orc_domain *d);
+/* Momentum-exchange force on the solid cells (Sec. 6, square cylinder), in
+ * lattice momentum per step, from the current post-collision state. */
+void   orc_drag(const orc_domain *d, double force[2]);
 void   orc_set_threads(int n);
 int    orc_get_threads(void);
 

@@ -6,7 +6,9 @@ relaxation rates, no moments).  Both the FP64 oracle and the CUDA library build
 their own initial populations from the (rho, ux, uy) fields given here.
 
 Sides are listed west, east, south, north as (kind, u_wall, v_wall) with kind
-0 = periodic, 1 = stationary wall, 2 = moving wall.  Arrays are (ny, nx), x fastest.
+0 = periodic, 1 = stationary wall, 2 = moving wall, 3 = parabolic velocity inlet
+(west side, u_wall = peak speed), 4 = convective outlet (east side, u_wall =
+convection speed).  Arrays are (ny, nx), x fastest.
 All random numbers come from ``numpy.random.default_rng(seed)``.
 """
 from __future__ import annotations
@@ -16,7 +18,7 @@ from typing import Optional
 
 import numpy as np
 
-PERIODIC, WALL, MOVING_WALL = 0, 1, 2
+PERIODIC, WALL, MOVING_WALL, INLET, OUTLET = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -212,3 +214,42 @@ def poisson_requests(count: int = 2000, rate: float = 200.0, seed: int = 0, U: f
                                  xc=H // 2)
         out.append((float(t[i]), c))
     return out
+
+
+def open_channel(nx: int, ny: int, nu: float, gamma: float, U_max: float = 0.05) -> Case:
+    """Channel between stationary walls at y = -1/2 and ny - 1/2 with a parabolic
+    velocity inlet of peak U_max on the west side and a convective outlet
+    (convection speed U_max) on the east side, fluid initially at rest."""
+    sides = ((INLET, U_max, 0.0), (OUTLET, U_max, 0.0), (WALL, 0.0, 0.0), (WALL, 0.0, 0.0))
+    return Case(f"openchannel{nx}x{ny}", nx, ny, nu, gamma, sides, U=U_max, meta={"U_max": U_max})
+
+
+def square_cylinder(D: int = 10, Re: float = 20.0, U_max: float = 0.1, gamma: float = 0.5,
+                    length: float = 50.0, height: float = 8.0, upstream: float = 12.5) -> Case:
+    """Flow past a square cylinder in a channel (Sec. 6): channel length 50 D and
+    height 8 D, cylinder of side D centred on the channel axis at 12.5 D from
+    the inlet, parabolic inflow of peak U_max, convective outflow, stationary
+    walls; nu = U_max D / Re.  The solid cells are the D x D block whose
+    half-way surfaces lie at xc +- D/2, yc +- D/2 (xc, yc on cell faces)."""
+    nx, ny = int(round(length * D)), int(round(height * D))
+    nu = U_max * D / Re
+    x0 = int(round(upstream * D - D / 2.0))
+    y0 = ny // 2 - D // 2
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[y0:y0 + D, x0:x0 + D] = 1
+    sides = ((INLET, U_max, 0.0), (OUTLET, U_max, 0.0), (WALL, 0.0, 0.0), (WALL, 0.0, 0.0))
+    return Case(f"squarecyl_D{D}_Re{Re:g}_g{gamma:g}", nx, ny, nu, gamma, sides, U=U_max, solid=solid,
+                meta={"Re": Re, "D": D, "x_front": x0 - 0.5, "x_rear": x0 + D - 0.5,
+                      "y_axis": ny / 2.0 - 0.5, "U_max": U_max})
+
+
+def periodic_obstacle(n: int = 48, D: int = 8, nu: float = 0.05, gamma: float = 0.5,
+                      Fx: float = 2e-6) -> Case:
+    """Fully periodic box with a square solid block of side D and a uniform body
+    force F_x on the fluid (no walls: at steady state the force on the block
+    balances the force on the fluid)."""
+    solid = np.zeros((n, n), dtype=np.uint8)
+    c0 = n // 2 - D // 2
+    solid[c0:c0 + D, c0:c0 + D] = 1
+    return Case(f"periodicobstacle{n}_D{D}", n, n, nu, gamma, periodic_sides(), Fx=Fx, solid=solid,
+                meta={"D": D})
