@@ -50,11 +50,37 @@ typedef enum {
     LBM_ERR_IO = -7              /* checkpoint file could not be read/written   */
 } lbm_status;
 
-typedef enum { LBM_SIDE_PERIODIC = 0, LBM_SIDE_WALL = 1, LBM_SIDE_MOVING_WALL = 2 } lbm_side_kind;
+/* Side kinds.  The two open kinds are those of the square-cylinder channel of
+ * Sec. 6:
+ *   LBM_SIDE_INLET  (west side only) fully developed parabolic velocity
+ *                   profile u(y) = 4 U (y + 1/2)(ny - y - 1/2) / ny^2 between
+ *                   walls at y = -1/2 and ny - 1/2, U = ux (|U| < 0.5),
+ *                   imposed by half-way bounce-back with the moving-wall term
+ *                   (rho0 = 1), u taken where the link crosses the inlet plane;
+ *   LBM_SIDE_OUTLET (east side only) convective outflow d_t u + U d_x u = 0 of
+ *                   Sec. 6 with U = ux (0 <= U <= 1): a ghost column at x = nx
+ *                   carries a velocity advanced by that equation (explicit,
+ *                   upwind, unit lattice steps) and supplies the populations
+ *                   entering the domain as the equilibrium (Eq. 15) at the
+ *                   reference density rho0 = 1 and that velocity plus the last
+ *                   column's non-equilibrium part (the reference density fixes
+ *                   the pressure level).  The ghost column starts from the last
+ *                   column's velocity whenever the populations are set
+ *                   (lbm_init_fields, lbm_set_populations, a storage change) and
+ *                   is carried by checkpoints.
+ * Open-sided domains are stepped by lbm_step; batches refuse them. */
+typedef enum {
+    LBM_SIDE_PERIODIC = 0,
+    LBM_SIDE_WALL = 1,
+    LBM_SIDE_MOVING_WALL = 2,
+    LBM_SIDE_INLET = 3,
+    LBM_SIDE_OUTLET = 4
+} lbm_side_kind;
 
 typedef struct {
-    int kind;          /* lbm_side_kind                                     */
-    double ux, uy;     /* wall velocity (LBM_SIDE_MOVING_WALL only)         */
+    int kind;          /* lbm_side_kind                                              */
+    double ux, uy;     /* wall velocity (MOVING_WALL); peak speed (INLET, ux);       */
+                       /* convection speed (OUTLET, ux)                              */
 } lbm_side;
 
 /* Opposite sides must both be periodic or both non-periodic.  A link whose
@@ -144,6 +170,16 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f);
 
 lbm_status lbm_steps_done(lbm_ctx *ctx, long *steps);
 lbm_status lbm_guard_count(lbm_ctx *ctx, long *count);
+
+/* Momentum-exchange force on the solid cells of the mask (Sec. 6, square
+ * cylinder; the standard method the paper names): over every link from a
+ * fluid cell x to a solid cell x + e_a, the post-collision population f~_a(x),
+ * which half-way bounce-back returns at the next step, hands the solid
+ * 2 e_a f~_a(x).  force (caller-owned, 2 doubles) receives the sum in lattice
+ * momentum per step of the current state, in FP64.  The preconditioned
+ * momentum equation carries every flux divided by gamma (Eq. 1), so the
+ * physical force is gamma times this value: C_D = 2 gamma force[0] / (rho0 U^2 D). */
+lbm_status lbm_drag(lbm_ctx *ctx, double force[2]);
 
 /* Failure-path self-test (no counterpart in the paper).  Every mbarrier wait of
  * the step kernels gives up after 2 s, raises the context's device error flag

@@ -87,6 +87,7 @@ struct lbm_ctx {
     CUtensorMap tload[2];        // TMA load descriptors of f[0], f[1]
     CUtensorMap tstore[2];       // TMA store descriptors of f[0], f[1]
     double *h_result = nullptr;  // pinned, 5 doubles
+    void *d_ghost[2] = {nullptr, nullptr};  // convective outlet ghost column of f[0], f[1] ([5][ny])
     void *d_stage = nullptr;     // grow-only device staging for field and population transfers
     size_t stage_bytes = 0;
     int res_blocks = 1;
@@ -138,6 +139,12 @@ StepParams make_params(const lbm_ctx *c)
         p.side_u[s][0] = moving ? c->sides[s].ux : 0.0;
         p.side_u[s][1] = moving ? c->sides[s].uy : 0.0;
     }
+    // open sides: the inlet's peak speed rides in side_u[west]
+    p.inlet = c->sides[0].kind == LBM_SIDE_INLET;
+    p.outlet = c->sides[1].kind == LBM_SIDE_OUTLET;
+    if (p.inlet) p.side_u[0][0] = c->sides[0].ux;
+    p.ghost_in = c->d_ghost[c->cur];
+    p.ghost_out = c->d_ghost[1 - c->cur];
     p.Fx = c->Fx;
     p.Fy = c->Fy;
     p.force = c->d_force;
@@ -147,6 +154,9 @@ StepParams make_params(const lbm_ctx *c)
     p.work = c->d_work;
     p.cf.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
     p.cd.set(c->gamma, c->omega, c->gi_mode, c->Fx, c->Fy, p.side_u);
+    const double out_u = p.outlet ? c->sides[1].ux : 0.0;
+    p.cf.set_open(c->ny, out_u);
+    p.cd.set_open(c->ny, out_u);
     p.c2.set(p.cf);
     p.nstrips = (c->nx + strip_width(c->storage) - 1) / strip_width(c->storage);
     const int bps = step_blocks_per_sm(c, p);
@@ -256,6 +266,8 @@ void free_ctx(lbm_ctx *c)
     dev_free(c->d_err);
     dev_free(c->d_work);
     dev_free(c->d_stage);
+    dev_free(c->d_ghost[0]);
+    dev_free(c->d_ghost[1]);
     if (c->h_result) cudaFreeHost(c->h_result);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -272,6 +284,16 @@ void *stage_buffer(lbm_ctx *c, size_t bytes)
     c->d_stage = dev_alloc(bytes);
     c->stage_bytes = c->d_stage ? bytes : 0;
     return c->d_stage;
+}
+
+// Outlet ghost column of the current state from its last column (a no-op
+// without an outlet).
+lbm_status outlet_reseed(lbm_ctx *c)
+{
+    if (!c->d_ghost[0]) return LBM_OK;
+    StepParams p = make_params(c);
+    LBM_CUDA(launch_outlet_seed(p, c->storage, c->f[c->cur], c->d_ghost[c->cur], c->stream));
+    return LBM_OK;
 }
 
 lbm_status snapshot_reset(lbm_ctx *c)
@@ -317,10 +339,20 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const l
         sides[2] = bnd->south;
         sides[3] = bnd->north;
         for (int s = 0; s < 4; ++s)
-            if (sides[s].kind < 0 || sides[s].kind > 2) return fail(LBM_ERR_INVALID, "bad side kind");
+            if (sides[s].kind < 0 || sides[s].kind > 4) return fail(LBM_ERR_INVALID, "bad side kind");
         if ((sides[0].kind == LBM_SIDE_PERIODIC) != (sides[1].kind == LBM_SIDE_PERIODIC) ||
             (sides[2].kind == LBM_SIDE_PERIODIC) != (sides[3].kind == LBM_SIDE_PERIODIC))
             return fail(LBM_ERR_INVALID, "opposite sides must both be periodic or both walls");
+        for (int s = 0; s < 4; ++s) {
+            if (sides[s].kind == LBM_SIDE_INLET && s != 0)
+                return fail(LBM_ERR_INVALID, "an inlet must be the west side");
+            if (sides[s].kind == LBM_SIDE_OUTLET && s != 1)
+                return fail(LBM_ERR_INVALID, "an outlet must be the east side");
+        }
+        if (sides[0].kind == LBM_SIDE_INLET && !(fabs(sides[0].ux) < 0.5))
+            return fail(LBM_ERR_INVALID, "inlet peak speed must be below 0.5");
+        if (sides[1].kind == LBM_SIDE_OUTLET && !(sides[1].ux >= 0.0 && sides[1].ux <= 1.0))
+            return fail(LBM_ERR_INVALID, "outlet convection speed must be in [0, 1]");
     } else {
         sides[0] = sides[1] = sides[2] = lbm_side{LBM_SIDE_WALL, 0.0, 0.0};
         sides[3] = lbm_side{LBM_SIDE_MOVING_WALL, U, 0.0};
@@ -362,8 +394,12 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const l
     c->d_guard = (unsigned long long *)dev_alloc(sizeof(unsigned long long));
     c->d_err = (int *)dev_alloc(sizeof(int));
     c->d_work = (unsigned int *)dev_alloc(2 * sizeof(unsigned int));
+    if (sides[1].kind == LBM_SIDE_OUTLET) {
+        c->d_ghost[0] = dev_alloc((size_t)5 * ny * sizeof(double));
+        c->d_ghost[1] = dev_alloc((size_t)5 * ny * sizeof(double));
+    }
     if (!c->f[0] || !c->f[1] || !c->d_snap_ux || !c->d_snap_uy || !c->d_partials || !c->d_result || !c->d_guard ||
-        !c->d_err || !c->d_work) {
+        !c->d_err || !c->d_work || (sides[1].kind == LBM_SIDE_OUTLET && (!c->d_ghost[0] || !c->d_ghost[1]))) {
         free_ctx(c);
         return fail(LBM_ERR_OOM, "device allocation failed");
     }
@@ -485,6 +521,9 @@ lbm_status lbm_set_option(lbm_ctx *c, const char *key, double v)
         c->cur = 0;
         e = build_tensor_maps(c);
         if (e != cudaSuccess) return cuda_fail(e, "cuTensorMapEncodeTiled");
+        // the ghost column holds the compute precision of the new storage
+        lbm_status so = outlet_reseed(c);
+        if (so != LBM_OK) return so;
     } else {
         return fail(LBM_ERR_INVALID, "unknown option: " + k);
     }
@@ -558,7 +597,9 @@ lbm_status lbm_init_fields(lbm_ctx *c, const double *rho, const double *ux, cons
     }
     StepParams p = make_params(c);
     LBM_CUDA(launch_init_eq(p, c->storage, dptr[0], dptr[1], dptr[2], c->f[c->cur], c->stream));
-    lbm_status s = snapshot_reset(c);
+    lbm_status s = outlet_reseed(c);
+    if (s != LBM_OK) return s;
+    s = snapshot_reset(c);
     if (s != LBM_OK) return s;
     LBM_CUDA(cudaStreamSynchronize(c->stream));
     c->steps = 0;
@@ -574,6 +615,8 @@ lbm_status lbm_step(lbm_ctx *c, long n)
     const int grid = step_grid(c, p);
     for (long i = 0; i < n; ++i) {
         p.step = (unsigned int)c->steps;  // seeds the stochastic rounding of 16-bit storage
+        p.ghost_in = c->d_ghost[c->cur];
+        p.ghost_out = c->d_ghost[1 - c->cur];
         cudaError_t e = launch_step(c, p, grid);
         if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
         c->cur = 1 - c->cur;
@@ -689,8 +732,23 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
     LBM_CUDA(cudaMemcpyAsync(d, f, 9 * N * 8, cudaMemcpyHostToDevice, c->stream));
     StepParams p = make_params(c);
     LBM_CUDA(launch_pops_from_f64(p, c->storage, d, c->f[c->cur], c->stream));
+    lbm_status s = outlet_reseed(c);
+    if (s != LBM_OK) return s;
     LBM_CUDA(cudaStreamSynchronize(c->stream));
     return LBM_OK;
+}
+
+lbm_status lbm_drag(lbm_ctx *c, double force[2])
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!force) return fail(LBM_ERR_INVALID, "null output");
+    StepParams p = make_params(c);
+    LBM_CUDA(launch_drag(p, c->storage, c->f[c->cur], c->d_partials, c->res_blocks, c->d_result, c->stream));
+    LBM_CUDA(cudaMemcpyAsync(c->h_result, c->d_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    force[0] = c->h_result[0];
+    force[1] = c->h_result[1];
+    return check_device_error(c);
 }
 
 lbm_status lbm_steps_done(lbm_ctx *c, long *steps)
@@ -736,7 +794,8 @@ lbm_status lbm_bounded_wait_selftest(lbm_ctx *c, double *waited_s)
 
 // Checkpoint layout: 8-byte magic, then int32 {version, nx, ny, storage, gi_mode},
 // int64 steps, double {gamma, nu, omega3..8, Fx, Fy}, then nine planes of
-// nx*ny stored elements (rows packed).
+// nx*ny stored elements (rows packed); version 2 (domains with a convective
+// outlet) appends the outlet ghost column, 5 * ny values in the compute type.
 static const char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
 
 lbm_status lbm_save(lbm_ctx *c, const char *path)
@@ -748,14 +807,18 @@ lbm_status lbm_save(lbm_ctx *c, const char *path)
     LBM_CUDA(cudaStreamSynchronize(c->stream));
     LBM_CUDA(cudaMemcpy2D(h.data(), (size_t)c->nx * es, c->f[c->cur], (size_t)c->pitch * es, (size_t)c->nx * es,
                           (size_t)9 * c->ny, cudaMemcpyDeviceToHost));
+    const size_t gbytes = (size_t)5 * c->ny * (c->storage == LBM_STORAGE_F64 ? sizeof(double) : sizeof(float));
+    std::vector<unsigned char> gh(c->d_ghost[0] ? gbytes : 0);
+    if (!gh.empty()) LBM_CUDA(cudaMemcpy(gh.data(), c->d_ghost[c->cur], gbytes, cudaMemcpyDeviceToHost));
     FILE *fp = fopen(path, "wb");
     if (!fp) return fail(LBM_ERR_IO, std::string("cannot open ") + path);
-    int hdr[5] = {1, c->nx, c->ny, c->storage, c->gi_mode};
+    int hdr[5] = {gh.empty() ? 1 : 2, c->nx, c->ny, c->storage, c->gi_mode};
     long long steps = c->steps;
     double par[10] = {c->gamma, c->nu, c->omega[3], c->omega[4], c->omega[5], c->omega[6], c->omega[7], c->omega[8], c->Fx, c->Fy};
     bool ok = fwrite(kMagic, 1, 8, fp) == 8 && fwrite(hdr, sizeof(int), 5, fp) == 5 &&
               fwrite(&steps, sizeof(steps), 1, fp) == 1 && fwrite(par, sizeof(double), 10, fp) == 10 &&
-              fwrite(h.data(), 1, h.size(), fp) == h.size();
+              fwrite(h.data(), 1, h.size(), fp) == h.size() &&
+              (gh.empty() || fwrite(gh.data(), 1, gh.size(), fp) == gh.size());
     ok = (fclose(fp) == 0) && ok;
     if (!ok) return fail(LBM_ERR_IO, std::string("write failed: ") + path);
     return LBM_OK;
@@ -774,9 +837,13 @@ lbm_status lbm_load(lbm_ctx *c, const char *path)
     bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, kMagic, 8) == 0 &&
               fread(hdr, sizeof(int), 5, fp) == 5 && fread(&steps, sizeof(steps), 1, fp) == 1 &&
               fread(par, sizeof(double), 10, fp) == 10;
-    if (!ok || hdr[0] != 1) {
+    if (!ok || (hdr[0] != 1 && hdr[0] != 2)) {
         fclose(fp);
         return fail(LBM_ERR_IO, "not a checkpoint of this library");
+    }
+    if ((hdr[0] == 2) != (c->d_ghost[0] != nullptr)) {
+        fclose(fp);
+        return fail(LBM_ERR_INVALID, "checkpoint and context differ in their outlet side");
     }
     if (hdr[1] != c->nx || hdr[2] != c->ny) {
         fclose(fp);
@@ -794,6 +861,9 @@ lbm_status lbm_load(lbm_ctx *c, const char *path)
     const size_t es = storage_bytes(c->storage);
     std::vector<unsigned char> h((size_t)9 * c->nx * c->ny * es);
     ok = fread(h.data(), 1, h.size(), fp) == h.size();
+    const size_t gbytes = (size_t)5 * c->ny * (c->storage == LBM_STORAGE_F64 ? sizeof(double) : sizeof(float));
+    std::vector<unsigned char> gh(hdr[0] == 2 ? gbytes : 0);
+    if (ok && !gh.empty()) ok = fread(gh.data(), 1, gh.size(), fp) == gh.size();
     fclose(fp);
     if (!ok) return fail(LBM_ERR_IO, "truncated checkpoint");
     c->gi_mode = hdr[4];
@@ -805,6 +875,7 @@ lbm_status lbm_load(lbm_ctx *c, const char *path)
     LBM_CUDA(cudaStreamSynchronize(c->stream));
     LBM_CUDA(cudaMemcpy2D(c->f[c->cur], (size_t)c->pitch * es, h.data(), (size_t)c->nx * es, (size_t)c->nx * es,
                           (size_t)9 * c->ny, cudaMemcpyHostToDevice));
+    if (!gh.empty()) LBM_CUDA(cudaMemcpy(c->d_ghost[c->cur], gh.data(), gh.size(), cudaMemcpyHostToDevice));
     c->steps = (long)steps;
     return snapshot_reset(c);
 }

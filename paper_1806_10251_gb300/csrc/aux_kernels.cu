@@ -1,10 +1,12 @@
 // Auxiliary kernels: equilibrium initialisation, observed fields, the FP64
-// convergence residual, and population format conversions.
+// convergence residual, the outlet ghost column, the momentum-exchange force,
+// and population format conversions.
 #include <math.h>
 
 #include <type_traits>
 
 #include "d2q9_collide.cuh"
+#include "open_bc.cuh"
 
 namespace lbm {
 
@@ -357,6 +359,77 @@ cudaError_t launch_residual(const StepParams &p, int storage, const void *f, dou
     with_storage(storage, f, [&](auto *fp) {
         using ST = std::remove_const_t<std::remove_pointer_t<decltype(fp)>>;
         residual_pass1<ST><<<nblocks, RES_THREADS, 0, s>>>(p, fp, half_ig, snap_ux, snap_uy, partials);
+    });
+    residual_pass2<<<1, RES_THREADS, 0, s>>>(partials, nblocks, result);
+    return cudaGetLastError();
+}
+
+// ---- convective outlet: ghost column from the last column --------------------
+template <typename R, typename ST>
+__global__ void outlet_seed_kernel(const StepParams p, const Consts<R> c, const ST *__restrict__ f, R *ghost)
+{
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= p.ny) return;
+    const int x = p.nx - 1;
+    const size_t i = (size_t)y * p.pitch + x;
+    R g[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) g[a] = (R)ld64(f, (size_t)a * p.plane + i);
+    R Fx = (R)p.Fx, Fy = (R)p.Fy;
+    if (p.force) {
+        Fx = (R)p.force[i];
+        Fy = (R)p.force[(size_t)p.plane + i];
+    }
+    R drho, ux, uy;
+    cell_state(c, g, Fx, Fy, drho, ux, uy);
+    outlet_row(c, p.ny, y, g, drho, ux, uy, ux, uy, ghost);
+}
+
+cudaError_t launch_outlet_seed(const StepParams &p, int storage, const void *f, void *ghost, cudaStream_t s)
+{
+    const int grid = (p.ny + 127) / 128;
+    with_storage(storage, f, [&](auto *fp) {
+        using ST = std::remove_const_t<std::remove_pointer_t<decltype(fp)>>;
+        if constexpr (std::is_same_v<ST, double>)
+            outlet_seed_kernel<double, ST><<<grid, 128, 0, s>>>(p, p.cd, fp, static_cast<double *>(ghost));
+        else
+            outlet_seed_kernel<float, ST><<<grid, 128, 0, s>>>(p, p.cf, fp, static_cast<float *>(ghost));
+    });
+    return cudaGetLastError();
+}
+
+// ---- momentum-exchange force on the solid cells (Sec. 6, square cylinder) ------
+// A post-collision population f~_a(x) of a fluid cell heading into a solid cell
+// x + e_a returns in the opposite direction at the next streaming (half-way
+// bounce-back, stationary solid) and hands the solid 2 e_a f~_a(x); summed in
+// FP64 over every such link, one block per row (rows with a stride).
+template <typename ST>
+__global__ void drag_pass1(const StepParams p, const ST *__restrict__ f, double *partials)
+{
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int y = blockIdx.x; y < p.ny; y += gridDim.x)
+        for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
+            if (solid_at(p, x, y)) continue;
+            const size_t i = (size_t)y * p.pitch + x;
+            for (int a = 1; a < 9; ++a) {
+                int tx = x + cx(a), ty = y + cy(a);
+                if (p.perx) tx = tx < 0 ? tx + p.nx : (tx >= p.nx ? tx - p.nx : tx);
+                if (p.pery) ty = ty < 0 ? ty + p.ny : (ty >= p.ny ? ty - p.ny : ty);
+                if (tx < 0 || tx >= p.nx || ty < 0 || ty >= p.ny || !solid_at(p, tx, ty)) continue;
+                const double fa = weight(a) + ld64(f, (size_t)a * p.plane + i);
+                acc[0] += 2.0 * cx(a) * fa;
+                acc[1] += 2.0 * cy(a) * fa;
+            }
+        }
+    block_sum5<RES_THREADS>(acc, partials + (size_t)blockIdx.x * 5);
+}
+
+cudaError_t launch_drag(const StepParams &p, int storage, const void *f, double *partials, int nblocks,
+                        double *result, cudaStream_t s)
+{
+    with_storage(storage, f, [&](auto *fp) {
+        using ST = std::remove_const_t<std::remove_pointer_t<decltype(fp)>>;
+        drag_pass1<ST><<<nblocks, RES_THREADS, 0, s>>>(p, fp, partials);
     });
     residual_pass2<<<1, RES_THREADS, 0, s>>>(partials, nblocks, result);
     return cudaGetLastError();

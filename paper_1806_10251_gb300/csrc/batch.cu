@@ -679,7 +679,8 @@ lbm_status lbm_batch_submit(lbm_batch *b, const lbm_request *req, long *id)
     if (req->use_bnd) {
         const lbm_side *sd[4] = {&req->bnd.west, &req->bnd.east, &req->bnd.south, &req->bnd.north};
         for (int k = 0; k < 4; ++k)
-            if (sd[k]->kind < 0 || sd[k]->kind > 2) return bfail(LBM_ERR_INVALID, "bad side kind");
+            if (sd[k]->kind < 0 || sd[k]->kind > 2)
+                return bfail(LBM_ERR_INVALID, "bad side kind (a batch takes periodic, wall and moving-wall sides)");
         if ((sd[0]->kind == LBM_SIDE_PERIODIC) != (sd[1]->kind == LBM_SIDE_PERIODIC) ||
             (sd[2]->kind == LBM_SIDE_PERIODIC) != (sd[3]->kind == LBM_SIDE_PERIODIC))
             return bfail(LBM_ERR_INVALID, "opposite sides must both be periodic or both walls");

@@ -42,6 +42,9 @@ struct Consts {
     R a3, a4;                      // 2/(3 omega3), 2/(3 omega4)
     R Fx, Fy;                      // uniform force
     R wall6[4][2];                 // 6 u_wall of each side (west, east, south, north)
+    R c4;                          // 3 - 6/gamma + 4/gamma^2 (raw fourth-order equilibrium, u^4 term)
+    R inlet_k, H;                  // parabolic inlet: 4 / ny^2 and ny
+    R out_u;                       // convective outlet: convection speed
 
     void set(double g, const double w[9], int gi_mode, double fx, double fy, const double side_u[4][2])
     {
@@ -67,6 +70,18 @@ struct Consts {
         Fy = R(fy);
         for (int s = 0; s < 4; ++s)
             for (int d = 0; d < 2; ++d) wall6[s][d] = R(6.0 * side_u[s][d]);
+        c4 = R(3.0 - 6.0 / g + 4.0 / (g * g));
+        inlet_k = R(0);
+        H = R(0);
+        out_u = R(0);
+    }
+
+    // open sides (Sec. 6, square cylinder): channel height ny, outlet speed
+    void set_open(int ny, double outlet_u)
+    {
+        inlet_k = R(4.0 / ((double)ny * (double)ny));
+        H = R((double)ny);
+        out_u = R(outlet_u);
     }
 };
 
@@ -129,8 +144,16 @@ struct StepParams {
     double gamma;
     double w3, w4, w5, w6, w7, w8;
     // wall velocity of each side (west, east, south, north); zero for
-    // stationary walls and periodic sides
+    // stationary walls and periodic sides; the peak speed of a west inlet
     double side_u[4][2];
+    // open sides of a channel (Sec. 6, square cylinder): west parabolic
+    // velocity inlet, east convective outlet.  The outlet keeps a ghost column
+    // at x = nx, [5][ny] in the kernel's compute type: the ghost velocity
+    // (u_g, v_g) and the populations 3, 6, 7 that enter the domain; a launch
+    // reads ghost_in (the source state's) and writes ghost_out.
+    int inlet, outlet;
+    const void *ghost_in;
+    void *ghost_out;
     double Fx, Fy;           // uniform force
     const float *force;      // optional per-cell force: [2][ny][pitch] (fx, fy)
     const uint8_t *solid;    // optional mask [ny][pitch], 1 = solid
@@ -211,6 +234,12 @@ cudaError_t launch_residual(const StepParams &p, int storage, const void *f, dou
                             cudaStream_t s);
 int residual_blocks(const StepParams &p);
 cudaError_t launch_bounded_wait_selftest(int *error, unsigned long long *waited_ns, cudaStream_t s);
+// Outlet ghost column from the last column of f (velocity and incoming populations).
+cudaError_t launch_outlet_seed(const StepParams &p, int storage, const void *f, void *ghost, cudaStream_t s);
+// Momentum-exchange force on the solid cells: two FP64 sums into result[0..1]
+// (partials: nblocks rows of 2 doubles).
+cudaError_t launch_drag(const StepParams &p, int storage, const void *f, double *partials, int nblocks,
+                        double *result, cudaStream_t s);
 cudaError_t launch_convert(const StepParams &p, int from_storage, const void *fin, int to_storage,
                            void *fout, cudaStream_t s);
 cudaError_t launch_pops_to_f64(const StepParams &p, int storage, const void *f, double *out,

@@ -40,6 +40,7 @@
 #include <cuda.h>
 
 #include "d2q9_collide.cuh"
+#include "open_bc.cuh"
 
 namespace lbm {
 
@@ -271,14 +272,12 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
                 }
                 if (inside) {
                     g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + cc - ex]);
+                } else if (outx || outy) {
+                    g[a] = boundary_value<R>(p, c, a, ex, ey, sx, sy, outx, outy,
+                                             StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + cc]));
                 } else {
-                    // half-way bounce-back, moving wall: + 6 w_a rho0 (e_a . u_w)
-                    R bb = R(0);
-                    if (outx != outy) {
-                        const int side = outx ? (sx < 0 ? 0 : 1) : (sy < 0 ? 2 : 3);
-                        bb = R(weight(a)) * (R(ex) * c.wall6[side][0] + R(ey) * c.wall6[side][1]);
-                    }
-                    g[a] = StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + cc]) + bb;
+                    // a solid neighbour: half-way bounce-back from a stationary solid
+                    g[a] = StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + cc]);
                 }
             }
         };
@@ -302,15 +301,6 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
                     valid = xc >= 0 && xc < p.nx;
                 }
             }
-        };
-        // Moving-wall term of half-way bounce-back for direction a whose source
-        // (sx, sy) lies beyond the outx / outy side(s): 6 w_a rho0 (e_a . u_w);
-        // a source beyond two sides (a corner) sees a stationary wall.
-        auto bb_term = [&](int a, int ex, int ey, int sx, int sy, bool outx, bool outy) -> R {
-            if (outx == outy) return R(0);
-            const int side = outx ? (sx < 0 ? 0 : 1) : (sy < 0 ? 2 : 3);
-            const R w = a == 0 ? R(4.0 / 9.0) : (a <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
-            return w * (R(ex) * c.wall6[side][0] + R(ey) * c.wall6[side][1]);
         };
         // Row r (sources r - 1 .. r + 1 landed) for the lane's cell and the halo
         // columns.  FAST rows have no boundary logic at all; other rows of
@@ -347,8 +337,8 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
                             const bool outx = !p.perx && (sx < 0 || sx >= p.nx);
                             const bool outy = !p.pery && (sy < 0 || sy >= p.ny);
                             if (outx || outy)
-                                g[a] = StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + cc]) +
-                                       bb_term(a, ex, ey, sx, sy, outx, outy);
+                                g[a] = boundary_value<R>(p, c, a, ex, ey, sx, sy, outx, outy,
+                                                         StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + cc]));
                         }
                     }
                 }
@@ -380,8 +370,8 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
                         if (outx || outy) {
                             out = true;
                             const int oa = (int)((OPP_PACK >> (4 * h_a)) & 15u);
-                            v = StorageTraits<ST>::cvt(r0[oa * T::BWX + ch]) +
-                                bb_term(h_a, h_ex, h_ey, sx, sy, outx, outy);
+                            v = boundary_value<R>(p, c, h_a, h_ex, h_ey, sx, sy, outx, outy,
+                                                  StorageTraits<ST>::cvt(r0[oa * T::BWX + ch]));
                         }
                     }
                     if (!out) v = StorageTraits<ST>::cvt(src[h_a * T::BWX + ch - h_ex]);
@@ -507,6 +497,7 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
 #pragma unroll
             for (int a = 0; a < 9; ++a) out[a] = cur[a];
             collide_cell<R, MODE, FORCED>(out, drx, dry, Fx, Fy, c, p.guard != 0, p.guard_count);
+            if (!FAST && p.outlet && x == p.nx - 1 && cur_valid) outlet_update<R>(p, c, y, out, Fx, Fy);
             // stage the row (the previous row's store must have read the buffer)
             if (lane == 0) bulk_wait_read_0();
             __syncwarp();

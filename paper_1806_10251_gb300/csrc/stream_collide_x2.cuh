@@ -252,15 +252,6 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         }
         return true;
     };
-    // Moving-wall term of half-way bounce-back for direction a whose source
-    // (sx, sy) lies beyond the outx / outy side(s): 6 w_a rho0 (e_a . u_w);
-    // a source beyond two sides (a corner) sees a stationary wall.
-    auto bb_term = [&](int a, int ex, int ey, int sx, int sy, bool outx, bool outy) -> R {
-        if (outx == outy) return R(0);
-        const int side = outx ? (sx < 0 ? 0 : 1) : (sy < 0 ? 2 : 3);
-        const R wa = a == 0 ? R(4.0 / 9.0) : (a <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
-        return wa * (R(ex) * c.wall6[side][0] + R(ey) * c.wall6[side][1]);
-    };
     // General pull of gbar(xc, r) (one cell) with walls, solids and bounce-back.
     auto pull_general = [&](int xc, int r, R(&g)[9]) {
         const ST *rm = row_ptr(r - 1), *r0 = row_ptr(r), *rp = row_ptr(r + 1);
@@ -278,7 +269,10 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
                 inside = __ldg(p.solid + (size_t)wy * p.pitch + wx) == 0;
             }
             if (inside) g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + ck - ex]);
-            else g[a] = StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + ck]) + bb_term(a, ex, ey, sx, sy, outx, outy);
+            else if (outx || outy)
+                g[a] = boundary_value<R>(p, c, a, ex, ey, sx, sy, outx, outy,
+                                         StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + ck]));
+            else g[a] = StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + ck]);  // solid neighbour
         }
     };
     // One cell of a general row: populations and density (-1 if none).  xc
@@ -346,8 +340,9 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
                             const bool outx = !p.perx && (sx < 0 || sx >= p.nx);
                             const bool outy = !p.pery && (sy < 0 || sy >= p.ny);
                             if (outx || outy)
-                                comp(g[a], k) = StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + cc + k]) +
-                                                bb_term(a, ex, ey, sx, sy, outx, outy);
+                                comp(g[a], k) = boundary_value<R>(
+                                    p, c, a, ex, ey, sx, sy, outx, outy,
+                                    StorageTraits<ST>::cvt(r0[opposite(a) * T::BWX + cc + k]));
                         }
                     }
                 }
@@ -382,7 +377,8 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
                     if (outx || outy) {
                         out = true;
                         const int oa = (int)((OPP_PACK >> (4 * h_a)) & 15u);
-                        v = StorageTraits<ST>::cvt(r0[oa * T::BWX + ch]) + bb_term(h_a, h_ex, h_ey, sx, sy, outx, outy);
+                        v = boundary_value<R>(p, c, h_a, h_ex, h_ey, sx, sy, outx, outy,
+                                              StorageTraits<ST>::cvt(r0[oa * T::BWX + ch]));
                     }
                 }
                 if (!out) v = StorageTraits<ST>::cvt(src[h_a * T::BWX + ch - h_ex]);
@@ -526,6 +522,16 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
                 dry = half * (rn - rs);
             }
             collide_x2<MODE, FORCED, GUARD>(out, drx, dry, Fx, Fy, p.c2, p.guard != 0, p.guard_count);
+            if (!FAST && p.outlet) {
+                // convective outlet: the lane holding the last column advances its ghost row
+                const int k = p.nx - 1 - xe;
+                if ((k == 0 || k == 1) && (cur_valid >> k & 1)) {
+                    R gk[9];
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) gk[a] = comp(out[a], k);
+                    outlet_update<R>(p, c, y, gk, comp(Fx, k), comp(Fy, k));
+                }
+            }
             if (!FAST && cur_valid != 3) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k)

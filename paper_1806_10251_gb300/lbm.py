@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7
-SIDE_PERIODIC, SIDE_WALL, SIDE_MOVING_WALL = 0, 1, 2
+SIDE_PERIODIC, SIDE_WALL, SIDE_MOVING_WALL, SIDE_INLET, SIDE_OUTLET = 0, 1, 2, 3, 4
 STORAGE_F32, STORAGE_F16, STORAGE_BF16, STORAGE_F64 = 0, 1, 2, 3
 GI_UNCORRECTED, GI_CUBIC_ONLY, GI_FULL = 0, 1, 2
 FD_CENTRAL, FD_ISOTROPIC = 0, 1  # values of the "fd" option (density-gradient stencil)
@@ -97,6 +97,7 @@ SIGNATURES = {
     "lbm_set_populations": (ctypes.c_int, [_P, _P]),
     "lbm_steps_done": (ctypes.c_int, [_P, ctypes.POINTER(_L)]),
     "lbm_guard_count": (ctypes.c_int, [_P, ctypes.POINTER(_L)]),
+    "lbm_drag": (ctypes.c_int, [_P, _P]),
     "lbm_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "lbm_destroy": (None, [_P]),
@@ -314,6 +315,12 @@ class Solver:
         v = ctypes.c_long()
         check(lib().lbm_guard_count(self._h, ctypes.byref(v)))
         return v.value
+
+    def drag(self) -> np.ndarray:
+        """Momentum-exchange force on the solid cells (lattice momentum per step)."""
+        F = np.zeros(2)
+        check(lib().lbm_drag(self._h, _ptr(F)))
+        return F
 
     def bounded_wait_selftest(self):
         """Run lbm_bounded_wait_selftest; returns (status, seconds waited) without
