@@ -234,7 +234,7 @@ lbm_status lbm_kernel_launches(lbm_ctx *ctx, long *launches);
  * thread while the engine runs (lbm_batch_start) or between lbm_batch_run calls. */
 typedef struct lbm_batch lbm_batch;
 enum { LBM_REQ_QUEUED = 0, LBM_REQ_RUNNING = 1, LBM_REQ_CONVERGED = 2, LBM_REQ_NOT_CONVERGED = 3,
-       LBM_REQ_DIVERGED = 4, LBM_REQ_FAILED = 5 };
+       LBM_REQ_DIVERGED = 4, LBM_REQ_FAILED = 5, LBM_REQ_CANCELLED = 6 };
 typedef struct {
     int nx, ny;              /* >= 3                                                 */
     double nu, gamma, U;     /* as lbm_create                                        */
@@ -243,6 +243,12 @@ typedef struct {
     double fx, fy;           /* uniform body force                                   */
     double tol;              /* steady when r < tol between checks (> 0)              */
     long max_steps;          /* give up after this many steps (> 0)                  */
+    long check_every;        /* steps between this request's convergence checks:     */
+                             /* 0 = the batch's check_every, else rounded up to a    */
+                             /* multiple of it (a slow domain's residual is then     */
+                             /* taken over a longer interval, as lbm_run_to_steady   */
+                             /* with that check_every); a check is also made when     */
+                             /* max_steps is reached                                 */
 } lbm_request;
 typedef struct {
     int state;               /* LBM_REQ_*                                             */
@@ -253,20 +259,40 @@ typedef struct {
 
 /* storage: LBM_STORAGE_*; gi_mode: LBM_GI_*; hbm_budget_bytes bounds the sum of
  * the admitted requests' footprints (2 population buffers + residual snapshot
- * + mask).  Options: "check_every" (K, even, default 1000: steps between
- * convergence checks, one CUDA graph of K launches), "rows_per_item" (rows of
- * a warp's work item; 0 = chosen by timing a few steps whenever the running
- * work has changed by more than 2x), "stochastic_rounding" (as lbm_set_option,
- * default 1, for domains admitted afterwards).  The error status of create is
- * LBM_ERR_INVALID for bad arguments, LBM_ERR_CUDA without a device, LBM_ERR_OOM
- * when the batch's own tables cannot be allocated.  A request is initialised at
- * rest (rho = 1, u = 0); its step count includes autotuning steps. */
+ * + mask, + the window sums below).  Options: "check_every" (K, even, default
+ * 1000: steps between convergence checks, one CUDA graph of K launches),
+ * "rows_per_item" (rows of a warp's work item; 0 = chosen by timing a few
+ * steps whenever the running work has changed by more than 2x), "persistent"
+ * (-1, default: chosen by the same timing; 0: a launch per step and force
+ * variant, replayed from the tick's CUDA graph; 1: the persistent kernel, the
+ * steps between two velocity samples in one cooperative launch with a bounded
+ * grid barrier between steps, launched directly -- FP32/FP16/BF16 storage,
+ * full GI kernel, running domains of one force variant; otherwise per-step
+ * launches),
+ * "stochastic_rounding" (as lbm_set_option, default 1, for domains admitted
+ * afterwards), "average_samples" (M, set before the first submit; default 16
+ * for FP16/BF16 storage, 0 otherwise): the velocity of every domain is sampled
+ * M times per check interval (every K/M steps) and the convergence residual
+ * compares these window averages instead of single states; a finished request
+ * returns the velocity average of its last window (lbm_batch_fields: rho is the
+ * final state's).  Stochastic rounding leaves an unbiased noise on a 16-bit
+ * state near its steady state, which the average removes from the residual and
+ * the result.  The error status of create is LBM_ERR_INVALID for bad
+ * arguments, LBM_ERR_CUDA without a device, LBM_ERR_OOM when the batch's own
+ * tables cannot be allocated.  A request is initialised at rest (rho = 1,
+ * u = 0); its step count includes autotuning steps. */
 lbm_status lbm_batch_create(size_t hbm_budget_bytes, int storage, int gi_mode, lbm_batch **out);
 lbm_status lbm_batch_set_option(lbm_batch *b, const char *key, double value);
 lbm_status lbm_batch_submit(lbm_batch *b, const lbm_request *req, long *id);   /* non-blocking */
 lbm_status lbm_batch_poll(lbm_batch *b, long id, int *done, lbm_result *res);  /* done: finished */
 lbm_status lbm_batch_fields(lbm_batch *b, long id, double *rho, double *ux, double *uy);
 lbm_status lbm_batch_release(lbm_batch *b, long id);  /* frees a finished request's memory */
+/* Cancel a request: a queued one leaves the queue at once, a running one stops
+ * at the end of the engine tick in progress (a request that converges in that
+ * tick keeps its result); either ends LBM_REQ_CANCELLED and keeps its state
+ * until released.  The other requests are unaffected (their arithmetic does not
+ * depend on the mix).  LBM_ERR_INVALID for an unknown or finished request. */
+lbm_status lbm_batch_cancel(lbm_batch *b, long id);
 /* Run engine ticks on the calling thread until nothing is queued or running,
  * or wall_seconds (> 0) have passed. */
 lbm_status lbm_batch_run(lbm_batch *b, double wall_seconds);

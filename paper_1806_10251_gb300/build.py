@@ -24,8 +24,9 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
               "-I", INCLUDE]
 
 
-# variants.cu: storage types 0..3 (LBM_STORAGE_*) x groups 0..3 of variants
-VARIANT_MATRIX = [(st, part) for st in range(4) for part in range(4)]
+# variants.cu: storage types 0..3 (LBM_STORAGE_*) x groups 0..3 of variants, and
+# group 4 (the persistent batch kernel) for the packed storages 0..2
+VARIANT_MATRIX = [(st, part) for st in range(4) for part in range(4)] + [(st, 4) for st in range(3)]
 
 
 def _nvcc() -> str:

@@ -275,7 +275,8 @@ __device__ __forceinline__ void block_sum5(double (&v)[5], double *out)
 
 template <typename ST>
 __global__ void residual_pass1(const StepParams p, const ST *__restrict__ f, double half_ig,
-                               double *__restrict__ snap_ux, double *__restrict__ snap_uy, double *partials)
+                               double *__restrict__ snap_ux, double *__restrict__ snap_uy, double *partials,
+                               double *__restrict__ win, double inv_count)
 {
     // Per cell in the storage's compute precision R; each thread's sums over
     // the cells it meets in one row (at most nx / blockDim.x of them) are kept
@@ -315,7 +316,16 @@ __global__ void residual_pass1(const StepParams p, const ST *__restrict__ f, dou
                 const R jy = (q[2] - q[4]) + (q[5] + q[6]) - (q[7] + q[8]);
                 const R mx = jx - fx[j] * hig, my = jy - fy[j] * hig;
                 const R ir = recip_aux(R(1) + dr);
-                const R u = mx * ir, v = my * ir;
+                R u = mx * ir, v = my * ir;
+                const size_t c = (size_t)y * p.nx + x0 + j * blockDim.x;
+                if (win) {
+                    // the window average in place of the current velocity
+                    const size_t N = (size_t)p.nx * p.ny;
+                    u = (R)(win[c] * inv_count);
+                    v = (R)(win[N + c] * inv_count);
+                    win[c] = 0.0;
+                    win[N + c] = 0.0;
+                }
                 const R du = u - sx[j], dv = v - sy[j];
                 du2 += du * du + dv * dv;
                 u2 += u * u + v * v;
@@ -323,7 +333,6 @@ __global__ void residual_pass1(const StepParams p, const ST *__restrict__ f, dou
                 sjx += mx;
                 sjy += my;
                 ++cnt;
-                const size_t c = (size_t)y * p.nx + x0 + j * blockDim.x;
                 snap_ux[c] = (double)u;
                 snap_uy[c] = (double)v;
             }
@@ -353,14 +362,71 @@ int residual_blocks(const StepParams &p)
 
 cudaError_t launch_residual(const StepParams &p, int storage, const void *f, double *snap_ux,
                             double *snap_uy, double *partials, int nblocks, double *result,
-                            cudaStream_t s)
+                            cudaStream_t s, double *acc, double inv_count)
 {
     const double half_ig = 0.5 / p.gamma;
     with_storage(storage, f, [&](auto *fp) {
         using ST = std::remove_const_t<std::remove_pointer_t<decltype(fp)>>;
-        residual_pass1<ST><<<nblocks, RES_THREADS, 0, s>>>(p, fp, half_ig, snap_ux, snap_uy, partials);
+        residual_pass1<ST><<<nblocks, RES_THREADS, 0, s>>>(p, fp, half_ig, snap_ux, snap_uy, partials, acc,
+                                                          inv_count);
     });
     residual_pass2<<<1, RES_THREADS, 0, s>>>(partials, nblocks, result);
+    return cudaGetLastError();
+}
+
+// ---- batch: window sums of the velocity (reduced-precision averaging) --------
+// The work items of the batch step kernels (a strip of W columns x Ly rows of
+// one active domain), distributed over the grid's warps; each lane takes
+// columns lane, lane + 32, ... of its strip.  rho u = sum g e - F/(2 gamma).
+template <typename ST>
+__global__ void batch_accumulate_kernel(const BatchArgs a, int W)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int n_active = a.state->n_active, total = a.state->total_items;
+    for (int item = warp; item < total; item += nwarps) {
+        int lo = 0, hi = n_active;  // prefix[lo] <= item < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.prefix[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const DomainDesc &D = a.domains[a.active[lo]];
+        if (!D.acc) continue;
+        const StepParams &p = D.p;
+        const int local = item - a.prefix[lo];
+        const int x0 = (local % p.nstrips) * W, y0 = (local / p.nstrips) * p.Ly;
+        const int y1 = min(y0 + p.Ly, p.ny);
+        const ST *f = static_cast<const ST *>(D.f[a.parity]);
+        const size_t N = (size_t)p.nx * p.ny;
+        const double hig = 0.5 / p.gamma;
+        for (int y = y0; y < y1; ++y)
+            for (int x = x0 + lane; x < min(x0 + W, p.nx); x += 32) {
+                if (solid_at(p, x, y)) continue;
+                const size_t i = (size_t)y * p.pitch + x;
+                double g[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) g[k] = ld64(f, (size_t)k * p.plane + i);
+                const double rho = 1.0 + (g[0] + (g[1] + g[3]) + (g[2] + g[4]) + ((g[5] + g[6]) + (g[7] + g[8])));
+                const double jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]) - p.Fx * hig;
+                const double jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]) - p.Fy * hig;
+                const size_t c = (size_t)y * p.nx + x;
+                D.acc[c] += jx / rho;
+                D.acc[N + c] += jy / rho;
+            }
+    }
+}
+
+cudaError_t launch_batch_accumulate(int storage, const BatchArgs &a, int grid, cudaStream_t s)
+{
+    const int W = strip_width(storage);
+    switch (storage) {
+    case LBM_STORAGE_F16: batch_accumulate_kernel<__half><<<grid, 128, 0, s>>>(a, W); break;
+    case LBM_STORAGE_BF16: batch_accumulate_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(a, W); break;
+    case LBM_STORAGE_F64: batch_accumulate_kernel<double><<<grid, 128, 0, s>>>(a, W); break;
+    default: batch_accumulate_kernel<float><<<grid, 128, 0, s>>>(a, W); break;
+    }
     return cudaGetLastError();
 }
 

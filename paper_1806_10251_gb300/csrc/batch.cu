@@ -72,6 +72,11 @@ struct Slot {
     double tol = 0;
     long max_steps = 0;
     int res_blocks = 1;
+    int check_mult = 1;         // convergence check every check_mult ticks
+    int ticks_since_check = 0;
+    bool check_due = false;     // this tick ends with a check
+    double *acc = nullptr;      // velocity sums of the current check window ([2][N]), or null
+    int samples = 0;            // samples in acc
 };
 
 struct Pending {
@@ -83,6 +88,7 @@ struct Pending {
 struct Record {
     int slot = -1;
     int readers = 0;  // lbm_batch_fields calls reading the slot's buffers; release waits for 0
+    bool cancel = false;  // lbm_batch_cancel on a running request: stop at the next tick
     int state = LBM_REQ_QUEUED;
     long steps = 0;
     double residual = INFINITY;
@@ -97,6 +103,7 @@ struct lbm_batch {
     size_t budget = 0, used = 0;
     int max_slots = 1024;
     int check_every = 1000;
+    int avg_samples = -1;  // velocity samples per check interval (-1: 16 for 16-bit storage, else 0)
     int Ly_option = 0;
     int Ly = 24;
     bool tuned = false;
@@ -113,11 +120,15 @@ struct lbm_batch {
     int *h_active = nullptr, *h_prefix = nullptr;  // pinned
     BatchState *h_state = nullptr;                 // pinned
     unsigned int *d_work = nullptr;
+    unsigned int *d_ctl = nullptr;  // persistent kernel: item counters, barrier arrivals and generation
+    int persistent_option = -1;     // -1: chosen by the autotuner, 0: per-step launches, 1: persistent
+    int mode = 0;                   // current: 0 per-step launches, 1 persistent kernel
     int *d_err = nullptr;
     double *d_sums = nullptr, *d_partials = nullptr, *h_sums = nullptr;
     cudaStream_t stream = nullptr, io_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_K = 0;
+    int graph_M = 0;
     int graph_variants = 0;                 // bit 0: unforced launch captured, bit 1: forced launch
     int variants = 0;                       // the same bits for the current active set
     std::chrono::steady_clock::time_point t0;
@@ -144,11 +155,24 @@ double seconds(const lbm_batch *b)
 
 lbm_status bfail(lbm_status s, const std::string &m) { return set_error(s, m); }
 
+// Velocity samples per check interval: a reduced-precision batch averages the
+// velocity over the interval (stochastic rounding leaves an unbiased noise on
+// the state that the average takes out of the residual and the result).
+int samples_per_tick(const lbm_batch *b)
+{
+    const int m = b->avg_samples >= 0
+                      ? b->avg_samples
+                      : ((b->storage == LBM_STORAGE_F16 || b->storage == LBM_STORAGE_BF16) ? 16 : 0);
+    return m < b->check_every ? m : b->check_every;
+}
+
 size_t footprint(const lbm_batch *b, int nx, int ny, bool solid)
 {
     const size_t pitch = (size_t)(nx + 63) / 64 * 64;
     const size_t plane = pitch * ny;
-    return 2 * 9 * plane * storage_bytes(b->storage) + 2 * (size_t)nx * ny * sizeof(double) + (solid ? plane : 0);
+    const size_t snaps = samples_per_tick(b) > 0 ? 4 : 2;  // snapshot (+ window sums) in FP64
+    return 2 * 9 * plane * storage_bytes(b->storage) + snaps * (size_t)nx * ny * sizeof(double) +
+           (solid ? plane : 0);
 }
 
 void free_slot(Slot &s)
@@ -157,6 +181,7 @@ void free_slot(Slot &s)
     if (s.f[1]) cudaFree(s.f[1]);
     if (s.snap) cudaFree(s.snap);
     if (s.solid) cudaFree(s.solid);
+    if (s.acc) cudaFree(s.acc);
     s = Slot();
 }
 
@@ -184,8 +209,10 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     s.bytes = footprint(b, r.nx, r.ny, !q.solid.empty());
     const size_t pb = 9 * (size_t)s.plane * storage_bytes(b->storage);
     const size_t N = (size_t)r.nx * r.ny;
+    const bool avg = samples_per_tick(b) > 0;
     if (cudaMalloc(&s.f[0], pb) != cudaSuccess || cudaMalloc(&s.f[1], pb) != cudaSuccess ||
         cudaMalloc((void **)&s.snap, 2 * N * sizeof(double)) != cudaSuccess ||
+        (avg && cudaMalloc((void **)&s.acc, 2 * N * sizeof(double)) != cudaSuccess) ||
         (!q.solid.empty() && cudaMalloc((void **)&s.solid, (size_t)s.plane) != cudaSuccess)) {
         cudaGetLastError();
         free_slot(s);
@@ -244,6 +271,8 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     set_geometry(p, b->Ly, b->storage);
     s.tol = r.tol;
     s.max_steps = r.max_steps;
+    s.check_mult = r.check_every > b->check_every ? (int)((r.check_every + b->check_every - 1) / b->check_every) : 1;
+    s.ticks_since_check = 0;
     s.res_blocks = residual_blocks(p);
     // descriptor table entry
     DomainDesc &d = b->h_desc[si];
@@ -259,7 +288,10 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     d.f[1] = s.f[1];
     d.forced = r.fx != 0.0 || r.fy != 0.0;
     s.forced = d.forced != 0;
+    d.acc = s.acc;
+    s.samples = 0;
     cudaError_t e = cudaMemcpyAsync(b->d_desc + si, &d, sizeof(DomainDesc), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && s.acc) e = cudaMemsetAsync(s.acc, 0, 2 * N * sizeof(double), b->stream);
     if (e == cudaSuccess)
         e = launch_init_eq(p, b->storage, nullptr, nullptr, nullptr, s.f[b->parity], b->stream);
     if (e == cudaSuccess)
@@ -322,6 +354,17 @@ int build_active(lbm_batch *b, double &cells)
         std::lock_guard<std::mutex> lk(b->mu);
         // the unforced domains first, then the forced ones: each group is one
         // launch of its own kernel variant over a contiguous item range
+        // cancelled requests leave the active set here, between ticks
+        for (int k = 0; k < b->max_slots; ++k) {
+            Slot &s = b->slots[k];
+            if (!s.used || !s.running) continue;
+            Record &rec = b->records[s.id];
+            if (rec.cancel) {
+                s.running = false;
+                rec.state = LBM_REQ_CANCELLED;
+                rec.t_done = seconds(b);
+            }
+        }
         for (int pass = 0; pass < 2; ++pass) {
             for (int k = 0; k < b->max_slots; ++k) {
                 const Slot &s = b->slots[k];
@@ -363,6 +406,7 @@ BatchArgs batch_args(const lbm_batch *b, int parity, int k, bool forced)
     a.step0 = b->d_step0;
     a.k = k;
     a.forced = forced;
+    a.ctl = b->d_ctl;
     return a;
 }
 
@@ -377,6 +421,32 @@ void launch_batch_all(lbm_batch *b, int parity, int k, const int grid[2])
     for (int v = 0; v < 2; ++v)
         if (b->variants >> v & 1)
             launch_batch_step(b->storage, b->gi_mode, v == 1, batch_args(b, parity, k, v == 1), grid[v], b->stream);
+}
+
+// The persistent kernel serves the full GI kernel in the packed storages when
+// the running domains are all of one force variant.
+bool persistent_possible(const lbm_batch *b)
+{
+    return b->persistent_option != 0 && batch_persistent_supported(b->storage, b->gi_mode) &&
+           (b->variants == 1 || b->variants == 2);
+}
+
+int persistent_grid(const lbm_batch *b)
+{
+    return b->num_sms * batch_persistent_blocks_per_sm(b->storage, b->variants == 2);
+}
+
+// Steps k0 .. k0 + n - 1 of a tick that starts on buffer `parity`, in the
+// current mode: one persistent launch, or a launch per step and force variant.
+cudaError_t launch_steps(lbm_batch *b, int parity, int k0, int n, const int grid[2], int pgrid)
+{
+    if (b->mode == 1) {
+        const bool forced = b->variants == 2;
+        return launch_batch_persistent(b->storage, forced, batch_args(b, parity, k0, forced), k0, n, pgrid,
+                                       b->stream);
+    }
+    for (int k = k0; k < k0 + n; ++k) launch_batch_all(b, (parity + k) & 1, k, grid);
+    return cudaGetLastError();
 }
 
 // Set the rows per item of every running domain and re-upload their descriptors.
@@ -427,67 +497,125 @@ lbm_status autotune(lbm_batch *b)
     h = h < 1 ? 1 : (h > 16 ? 16 : h);
     int cand[3] = {h > 1 ? (h + 1) / 2 : 1, h, h < 16 ? 2 * h : 24};
     float best_ms = 1e30f;
-    int best = h;
+    int best = h, best_mode = 0;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LBM_ERR_CUDA;
     const int reps = 4;  // even: the parity is unchanged
     const int grid[2] = {batch_grid(b, false), batch_grid(b, true)};
+    {
+        double cells;
+        build_active(b, cells);  // the force variants present
+    }
+    const bool can_persist = persistent_possible(b);
+    const int pgrid = can_persist ? persistent_grid(b) : 0;
     int last = -1;
     for (int c : cand) {
         if (c == last) continue;
         last = c;
         apply_Ly(b, c);
-        double cells;
-        build_active(b, cells);
-        cudaEventRecord(e0, b->stream);
-        for (int r = 0; r < reps; ++r) launch_batch_all(b, (b->parity + r) & 1, r, grid);
-        cudaEventRecord(e1, b->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return LBM_ERR_CUDA;
-        }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        std::lock_guard<std::mutex> lk(b->mu);
-        b->launches += reps;
-        b->cell_updates += cells * reps;
-        for (int k = 0; k < b->max_slots; ++k)
-            if (b->slots[k].used && b->slots[k].running) b->records[b->slots[k].id].steps += reps;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
+        for (int mode = 0; mode < 2; ++mode) {
+            if (mode == 1 && !can_persist) continue;
+            if (b->persistent_option >= 0 && mode != b->persistent_option) continue;
+            b->mode = mode;
+            double cells;
+            build_active(b, cells);
+            cudaEventRecord(e0, b->stream);
+            cudaError_t le = launch_steps(b, b->parity, 0, reps, grid, pgrid);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return LBM_ERR_CUDA;
+            }
+            if (le != cudaSuccess) {  // a cooperative launch the device refuses: not a candidate
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            std::lock_guard<std::mutex> lk(b->mu);
+            b->launches += reps;
+            b->cell_updates += cells * reps;
+            for (int k = 0; k < b->max_slots; ++k)
+                if (b->slots[k].used && b->slots[k].running) b->records[b->slots[k].id].steps += reps;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+                best_mode = mode;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     apply_Ly(b, best);
+    b->mode = best_mode;
     b->tuned = true;
     b->tuned_strip_rows = rows;
     return LBM_OK;
 }
 
-lbm_status ensure_graph(lbm_batch *b)
+// The steps of one tick in segments that end at the velocity sample points
+// (a launch per step, or one persistent launch per segment), each sample an
+// accumulate launch over the active domains; recorded into the tick's graph
+// (per-step launches) or launched directly (persistent launches: a
+// cooperative launch is never recorded into a graph).
+cudaError_t issue_tick(lbm_batch *b, const int grid[2], int pgrid)
 {
-    if (b->graph && b->graph_K == b->check_every && b->graph_variants == b->variants) return LBM_OK;
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
+    const int M = samples_per_tick(b), K = b->check_every;
+    const int every = M > 0 ? K / M : K;  // steps between velocity samples
+    const int gacc = b->num_sms * 8;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < K && le == cudaSuccess;) {
+        const int n = (M > 0 && k / every < M) ? every : K - k;
+        le = launch_steps(b, b->parity, k, n, grid, pgrid);
+        k += n;
+        if (le == cudaSuccess && M > 0 && k % every == 0 && k / every <= M)
+            le = launch_batch_accumulate(b->storage, batch_args(b, (b->parity + k) & 1, k, false), gacc, b->stream);
     }
-    cudaGraph_t g = nullptr;
-    // occupancy queries before the capture starts
+    return le;
+}
+
+lbm_status capture_graph(lbm_batch *b)
+{
+    // occupancy queries (and shared-memory attributes) before the capture starts
     const int grid[2] = {batch_grid(b, false), batch_grid(b, true)};
+    cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
-    for (int k = 0; k < b->check_every; ++k) launch_batch_all(b, (b->parity + k) & 1, k, grid);
-    if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess) return LBM_ERR_CUDA;
+    const cudaError_t le = issue_tick(b, grid, 0);
+    const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
     const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         b->graph = nullptr;
+        cudaGetLastError();
         return LBM_ERR_CUDA;
     }
+    return LBM_OK;
+}
+
+// The graph of per-step launches for the current K, force variants and
+// samples (the persistent mode needs none).
+lbm_status ensure_graph(lbm_batch *b)
+{
+    const int M = samples_per_tick(b);
+    if (b->mode == 1 && !persistent_possible(b)) b->mode = 0;  // the active set no longer allows it
+    if (b->mode == 1) return LBM_OK;
+    if (b->graph && b->graph_K == b->check_every && b->graph_variants == b->variants && b->graph_M == M)
+        return LBM_OK;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    const lbm_status st = capture_graph(b);
+    if (st != LBM_OK) return st;
     b->graph_K = b->check_every;
     b->graph_variants = b->variants;
+    b->graph_M = M;
     return LBM_OK;
 }
 
@@ -510,15 +638,37 @@ lbm_status tick(lbm_batch *b, bool *busy)
         n = build_active(b, cells);
     }
     if (ensure_graph(b) != LBM_OK) return bfail(LBM_ERR_CUDA, "batch graph capture failed");
-    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
-    if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
-    // convergence residual of every running domain (FP64)
+    cudaError_t e;
+    if (b->mode == 1) {
+        const int grid[2] = {batch_grid(b, false), batch_grid(b, true)};
+        e = issue_tick(b, grid, persistent_grid(b));
+        if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+    } else {
+        e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    }
+    // convergence residual (FP64) of every running domain whose check is due:
+    // its own interval has passed, or its step budget ends with this tick
     for (int i = 0; i < n; ++i) {
         const int k = b->h_active[i];
         Slot &s = b->slots[k];
+        long steps_after;
+        {
+            std::lock_guard<std::mutex> lk(b->mu);
+            steps_after = b->records[s.id].steps + b->check_every;
+        }
+        s.ticks_since_check += 1;
+        if (s.acc) s.samples += samples_per_tick(b);
+        s.check_due = s.ticks_since_check >= s.check_mult || steps_after >= s.max_steps;
+        if (!s.check_due) continue;
+        s.ticks_since_check = 0;
         const size_t N = (size_t)s.nx * s.ny;
+        // a reduced-precision domain compares window averages (and keeps the
+        // last one in its snapshot as its result)
+        const bool avg = s.acc && s.samples > 0;
         e = launch_residual(s.p, b->storage, s.f[b->parity], s.snap, s.snap + N, b->d_partials, s.res_blocks,
-                            b->d_sums + 5 * k, b->stream);
+                            b->d_sums + 5 * k, b->stream, avg ? s.acc : nullptr, avg ? 1.0 / s.samples : 0.0);
+        if (avg) s.samples = 0;
         if (e != cudaSuccess) return bfail(LBM_ERR_CUDA, "batch residual launch failed");
     }
     cudaMemcpyAsync(b->h_sums, b->d_sums, (size_t)b->max_slots * 5 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -531,6 +681,7 @@ lbm_status tick(lbm_batch *b, bool *busy)
         // on the batch stream: later launches there see the cleared counters
         cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
         cudaMemsetAsync(b->d_work, 0, 2 * sizeof(unsigned int), b->stream);
+        cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), b->stream);
         cudaStreamSynchronize(b->stream);
         return bfail(LBM_ERR_CUDA, "a batched step kernel's bounded wait expired");
     }
@@ -544,6 +695,7 @@ lbm_status tick(lbm_batch *b, bool *busy)
         Slot &s = b->slots[k];
         Record &rec = b->records[s.id];
         rec.steps += b->check_every;
+        if (!s.check_due) continue;
         const double du2 = b->h_sums[5 * k], u2 = b->h_sums[5 * k + 1];
         double r;
         if (!isfinite(du2) || !isfinite(u2)) r = NAN;
@@ -619,6 +771,7 @@ lbm_status lbm_batch_create(size_t hbm_budget_bytes, int storage, int gi_mode, l
               cudaMallocHost((void **)&b->h_step0, (size_t)b->max_slots * sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc((void **)&b->d_state, sizeof(BatchState)) == cudaSuccess &&
               cudaMalloc((void **)&b->d_work, 2 * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_ctl, 4 * sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc((void **)&b->d_err, sizeof(int)) == cudaSuccess &&
               cudaMalloc((void **)&b->d_sums, (size_t)b->max_slots * 5 * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void **)&b->d_partials, 1024 * 5 * sizeof(double)) == cudaSuccess &&
@@ -628,6 +781,7 @@ lbm_status lbm_batch_create(size_t hbm_budget_bytes, int storage, int gi_mode, l
               cudaMallocHost((void **)&b->h_state, sizeof(BatchState)) == cudaSuccess;
     if (ok) {
         ok = cudaMemset(b->d_work, 0, 2 * sizeof(unsigned int)) == cudaSuccess &&
+             cudaMemset(b->d_ctl, 0, 4 * sizeof(unsigned int)) == cudaSuccess &&
              cudaMemset(b->d_err, 0, sizeof(int)) == cudaSuccess &&
              cudaMemset(b->d_sums, 0, (size_t)b->max_slots * 5 * sizeof(double)) == cudaSuccess;
         b->h_state->n_active = 0;
@@ -647,6 +801,20 @@ lbm_status lbm_batch_set_option(lbm_batch *b, const char *key, double v)
     if (!b || !key) return bfail(LBM_ERR_INVALID, "null argument");
     const std::string k(key);
     std::lock_guard<std::mutex> run_lock(b->run_mu);
+    if (k == "persistent") {
+        if (v != -1.0 && v != 0.0 && v != 1.0) return bfail(LBM_ERR_INVALID, "persistent must be -1, 0 or 1");
+        b->persistent_option = (int)v;  // run_mu held: not during a tick
+        b->mode = v == 1.0 ? 1 : 0;
+        b->tuned = false;
+        return LBM_OK;
+    }
+    if (k == "average_samples") {
+        if (v < 0 || v > 1024 || v != (double)(int)v) return bfail(LBM_ERR_INVALID, "average_samples must be 0..1024");
+        std::lock_guard<std::mutex> lk(b->mu);
+        if (!b->records.empty()) return bfail(LBM_ERR_INVALID, "average_samples must be set before the first submit");
+        b->avg_samples = (int)v;
+        return LBM_OK;
+    }
     if (k == "check_every") {
         const int K = (int)v;
         if (K < 2 || K % 2 || K > 100000) return bfail(LBM_ERR_INVALID, "check_every must be even, 2..100000");
@@ -676,6 +844,7 @@ lbm_status lbm_batch_submit(lbm_batch *b, const lbm_request *req, long *id)
     const double w = 1.0 / (3.0 * req->nu / req->gamma + 0.5);
     if (!(w > 0 && w < 2)) return bfail(LBM_ERR_INVALID, "omega4 out of (0, 2)");
     if (!(req->tol > 0) || req->max_steps <= 0) return bfail(LBM_ERR_INVALID, "tol and max_steps must be > 0");
+    if (req->check_every < 0) return bfail(LBM_ERR_INVALID, "check_every must be >= 0");
     if (req->use_bnd) {
         const lbm_side *sd[4] = {&req->bnd.west, &req->bnd.east, &req->bnd.south, &req->bnd.north};
         for (int k = 0; k < 4; ++k)
@@ -750,9 +919,12 @@ lbm_status lbm_batch_fields(lbm_batch *b, long id, double *rho, double *ux, doub
         st = bfail(LBM_ERR_OOM, "device allocation failed (fields)");
     } else {
         e = launch_fields(s.p, b->storage, s.f[parity], d, d + N, d + 2 * N, b->io_stream);
+        // a window-averaged domain returns the velocity average of its last check
+        // (held in the snapshot; solid cells keep the fields kernel's NaN)
+        const double *vu = s.acc ? s.snap : d + N, *vv = s.acc ? s.snap + N : d + 2 * N;
         if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, d, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
-        if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, d + N, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
-        if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, d + 2 * N, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
+        if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, vu, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
+        if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, vv, N * 8, cudaMemcpyDeviceToHost, b->io_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->io_stream);
         cudaFree(d);
         if (e != cudaSuccess) st = bfail(LBM_ERR_CUDA, std::string("batch fields: ") + cudaGetErrorString(e));
@@ -764,6 +936,34 @@ lbm_status lbm_batch_fields(lbm_batch *b, long id, double *rho, double *ux, doub
     }
     b->cv.notify_all();
     return st;
+}
+
+lbm_status lbm_batch_cancel(lbm_batch *b, long id)
+{
+    if (!b) return bfail(LBM_ERR_INVALID, "null batch");
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        auto it = b->records.find(id);
+        if (it == b->records.end()) return bfail(LBM_ERR_INVALID, "unknown request id");
+        Record &rec = it->second;
+        if (rec.state >= LBM_REQ_CONVERGED) return bfail(LBM_ERR_INVALID, "request already finished");
+        bool dequeued = false;
+        if (rec.state == LBM_REQ_QUEUED)
+            for (auto q = b->queue.begin(); q != b->queue.end(); ++q)
+                if (q->id == id) {
+                    b->queue.erase(q);
+                    dequeued = true;
+                    break;
+                }
+        if (dequeued) {
+            rec.state = LBM_REQ_CANCELLED;
+            rec.t_done = seconds(b);
+        } else {
+            rec.cancel = true;  // running, or being admitted: the engine retires it between ticks
+        }
+    }
+    b->cv.notify_all();
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_release(lbm_batch *b, long id)
@@ -868,6 +1068,7 @@ void lbm_batch_destroy(lbm_batch *b)
     if (b->h_step0) cudaFreeHost(b->h_step0);
     cudaFree(b->d_state);
     cudaFree(b->d_work);
+    cudaFree(b->d_ctl);
     cudaFree(b->d_err);
     cudaFree(b->d_sums);
     cudaFree(b->d_partials);

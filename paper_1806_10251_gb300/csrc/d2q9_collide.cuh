@@ -39,7 +39,8 @@ template <typename ST> struct StorageTraits;
 // constant forcing that the slowest viscous modes amplify by about
 // 1/(nu k^2).)  Values so small that the 16-bit result is subnormal would
 // drop more bits than r covers; FP16 storage is scaled so that only
-// |g| < 2^-28 gets there.
+// |g| < 2^-28 gets there.  (The packed kernels store pairs through the
+// hardware's stochastic conversion instead, PairIO in stream_collide_x2.cuh.)
 template <> struct StorageTraits<float> {
     using R = float;
     static constexpr bool kReduced = false;
@@ -56,11 +57,24 @@ template <> struct StorageTraits<double> {
     __device__ static __forceinline__ void store(double *p, double v) { *p = v; }
     __device__ static __forceinline__ void store_sr(double *p, double v, uint32_t) { *p = v; }
 };
+// FP16 value h of F16_SCALE * g -> g in FP32 by one mixed-precision FMA,
+// h * 2^-14 + (-0): exact (2^-14 is an FP16 normal and the product of two FP16
+// values is exact in FP32), the same value as converting and then scaling.
+__device__ __forceinline__ float f16_unscaled(__half h)
+{
+    static_assert(F16_INV_SCALE == 1.0f / 16384.0f, "the FMA constant below is 2^-14");
+    float d;
+    asm("{.reg .f16 s; mov.b16 s, 0x0400; fma.rn.f32.f16 %0, %1, s, %2;}"
+        : "=f"(d)
+        : "h"(__half_as_ushort(h)), "f"(-0.0f));
+    return d;
+}
+
 template <> struct StorageTraits<__half> {  // holds F16_SCALE * g
     using R = float;
     static constexpr bool kReduced = true;
-    __device__ static __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)) * F16_INV_SCALE; }
-    __device__ static __forceinline__ float cvt(__half v) { return __half2float(v) * F16_INV_SCALE; }
+    __device__ static __forceinline__ float load(const __half *p) { return f16_unscaled(__ldg(p)); }
+    __device__ static __forceinline__ float cvt(__half v) { return f16_unscaled(v); }
     __device__ static __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v * F16_SCALE); }
     __device__ static __forceinline__ void store_sr(__half *p, float v, uint32_t r)
     {

@@ -124,4 +124,38 @@ LBM_STORAGE_ENTRY(f16, __half)
 LBM_STORAGE_ENTRY(bf16, __nv_bfloat16)
 LBM_STORAGE_ENTRY(f64, double)
 
+bool batch_persistent_supported(int storage, int gi_mode)
+{
+    return storage != LBM_STORAGE_F64 && gi_mode == LBM_GI_FULL;
+}
+
+cudaError_t launch_batch_persistent(int storage, bool forced, const BatchArgs &a, int k0, int nsteps, int grid,
+                                    cudaStream_t s)
+{
+#define LBM_PERSISTENT(ST) \
+    (forced ? batch_persistent_variant_launch<ST, true>(a, k0, nsteps, grid, s) \
+            : batch_persistent_variant_launch<ST, false>(a, k0, nsteps, grid, s))
+    switch (storage) {
+    case LBM_STORAGE_F16: return LBM_PERSISTENT(__half);
+    case LBM_STORAGE_BF16: return LBM_PERSISTENT(__nv_bfloat16);
+    case LBM_STORAGE_F32: return LBM_PERSISTENT(float);
+    default: return cudaErrorNotSupported;
+    }
+#undef LBM_PERSISTENT
+}
+
+int batch_persistent_blocks_per_sm(int storage, bool forced)
+{
+    switch (storage) {
+    case LBM_STORAGE_F16:
+        return forced ? batch_persistent_variant_blocks<__half, true>() : batch_persistent_variant_blocks<__half, false>();
+    case LBM_STORAGE_BF16:
+        return forced ? batch_persistent_variant_blocks<__nv_bfloat16, true>()
+                      : batch_persistent_variant_blocks<__nv_bfloat16, false>();
+    case LBM_STORAGE_F32:
+        return forced ? batch_persistent_variant_blocks<float, true>() : batch_persistent_variant_blocks<float, false>();
+    default: return 0;
+    }
+}
+
 }  // namespace lbm

@@ -183,6 +183,7 @@ struct alignas(128) DomainDesc {
     StepParams p;           // the domain's parameters (work/error pointers unused)
     const void *f[2];       // population buffers
     int forced;             // nonzero: a body force acts (uniform Fx, Fy)
+    double *acc;            // velocity sums for the check-window average ([2][nx*ny]), or null
 };
 
 // Active set of a batch, read by the kernel each launch (so a captured graph
@@ -204,6 +205,7 @@ struct BatchArgs {
     const unsigned int *step0;  // per active index: the domain's step count at the start of the tick
     int forced;                 // this launch covers the forced domains (items split .. total) or the others
     int k;                      // launch index within the tick (domain step = step0 + k)
+    unsigned int *ctl;          // persistent kernel: {items of even steps, of odd steps, arrivals, generation}
 };
 
 // The launchers below are defined per storage type (one translation unit each).
@@ -215,6 +217,14 @@ cudaError_t launch_step_bf16(const StepParams &p, const CUtensorMap &tin, const 
 cudaError_t launch_step_f64(const StepParams &p, const CUtensorMap &tin, const CUtensorMap &tout, const void *fin, void *fout, int grid, cudaStream_t s);
 cudaError_t launch_batch_step(int storage, int gi_mode, bool forced, const BatchArgs &a, int grid, cudaStream_t s);
 int batch_blocks_per_sm(int storage, int gi_mode, bool forced);
+// The persistent batch kernel (FP32/FP16/BF16 storage, full GI kernel, one force
+// variant): steps k0 .. k0 + nsteps - 1 of the tick (parity a.parity + k) in one
+// cooperative launch of `grid` blocks (at most the resident count) with a
+// bounded grid barrier between steps.
+bool batch_persistent_supported(int storage, int gi_mode);
+cudaError_t launch_batch_persistent(int storage, bool forced, const BatchArgs &a, int k0, int nsteps, int grid,
+                                    cudaStream_t s);
+int batch_persistent_blocks_per_sm(int storage, bool forced);
 int blocks_per_sm_f32(int gi_mode, bool forced);
 int blocks_per_sm_f16(int gi_mode, bool forced);
 int blocks_per_sm_bf16(int gi_mode, bool forced);
@@ -229,9 +239,14 @@ cudaError_t launch_init_eq(const StepParams &p, int storage, const double *rho, 
                            const double *uy, void *f, cudaStream_t s);
 cudaError_t launch_fields(const StepParams &p, int storage, const void *f, double *rho, double *ux,
                           double *uy, cudaStream_t s);
+// acc (optional, [2][nx*ny]): the velocity entering the residual is acc *
+// inv_count (a window average) instead of the current one; acc is zeroed.
 cudaError_t launch_residual(const StepParams &p, int storage, const void *f, double *snap_ux,
                             double *snap_uy, double *partials, int nblocks, double *result,
-                            cudaStream_t s);
+                            cudaStream_t s, double *acc = nullptr, double inv_count = 0.0);
+// Add the current velocity of every active domain of a batch to its window sums
+// (DomainDesc::acc), reading the population buffer `a.parity`.
+cudaError_t launch_batch_accumulate(int storage, const BatchArgs &a, int grid, cudaStream_t s);
 int residual_blocks(const StepParams &p);
 cudaError_t launch_bounded_wait_selftest(int *error, unsigned long long *waited_ns, cudaStream_t s);
 // Outlet ghost column from the last column of f (velocity and incoming populations).

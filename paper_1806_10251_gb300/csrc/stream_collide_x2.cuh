@@ -60,30 +60,37 @@ template <> struct PairIO<float> {
     __device__ static __forceinline__ void stg2_sr(float *p, F2 v, uint32_t) { stg2(p, v); }
     static constexpr uint32_t HALF_ULP = 0u;
 };
+// 16-bit pairs are rounded by the hardware's stochastic conversion
+// (cvt.rs.{f16x2,bf16x2}.f32 d, hi, lo, rbits): the low half of d (the even
+// cell) adds rbits[12:0] (FP16) or rbits[15:0] (BF16) to the mantissa bits it
+// drops, the high half (the odd cell) rbits[28:16] or rbits[31:16], and both
+// truncate -- unbiased, in the FP16 subnormal range as well.  From 32 random
+// bits r the pair takes rbits = r ^ (r >> 16), so that the even cell's field
+// depends on the high bits of r too.
+__device__ __forceinline__ uint32_t sr_fold(uint32_t r) { return r ^ (r >> 16); }
+
 template <> struct PairIO<__half> {  // holds F16_SCALE * g
-    __device__ static __forceinline__ F2 from_h2(__half2 h)
+    // one mixed-precision FMA per value: the conversion and the inverse scale
+    __device__ static __forceinline__ float from_h(__half h) { return f16_unscaled(h); }
+    __device__ static __forceinline__ F2 lds2(const __half *p)
     {
-        const float2 f = __half22float2(h);
-        return F2{f.x, f.y} * f2(F16_INV_SCALE);
+        const __half2 h = *reinterpret_cast<const __half2 *>(p);
+        return F2{from_h(__low2half(h)), from_h(__high2half(h))};
     }
-    __device__ static __forceinline__ F2 lds2(const __half *p) { return from_h2(*reinterpret_cast<const __half2 *>(p)); }
-    __device__ static __forceinline__ F2 join(__half a, __half b) { return from_h2(__halves2half2(a, b)); }
+    __device__ static __forceinline__ F2 join(__half a, __half b) { return F2{from_h(a), from_h(b)}; }
     __device__ static __forceinline__ void stg2(__half *p, F2 v)
     {
         const F2 s = v * f2(F16_SCALE);
         *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(s.x, s.y);
     }
-    // r: 32 random bits; the even cell takes bits 19..31, the odd cell bits
-    // 6..18 (13 dropped bits each for a normal FP16 result); one truncating
-    // conversion packs both.  HALF_ULP in place of random bits adds half of the
-    // dropped range: rounding to nearest, ties away from zero.
-    static constexpr uint32_t HALF_ULP = 0x80040000u;
+    // HALF_ULP in place of random bits folds to rbits = 0x10001000: half of the
+    // dropped range in both cells, i.e. rounding to nearest, ties away from zero.
+    static constexpr uint32_t HALF_ULP = 0x10000000u;
     __device__ static __forceinline__ void stg2_sr(__half *p, F2 v, uint32_t r)
     {
         const F2 s = v * f2(F16_SCALE);
-        const uint32_t lo = __float_as_uint(s.x) + (r >> 19), hi = __float_as_uint(s.y) + ((r >> 6) & 0x1fffu);
         uint32_t d;
-        asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(s.y), "f"(s.x), "r"(sr_fold(r)));
         *reinterpret_cast<uint32_t *>(p) = d;
     }
 };
@@ -105,15 +112,12 @@ template <> struct PairIO<__nv_bfloat16> {
     {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
     }
-    // r: 32 random bits; the even cell takes the upper 16, the odd cell the
-    // lower 16 (16 dropped bits each); one truncating conversion packs both.
-    // HALF_ULP: rounding to nearest, ties away from zero.
-    static constexpr uint32_t HALF_ULP = 0x80008000u;
+    // HALF_ULP folds to rbits = 0x80008000: rounding to nearest, ties away from zero.
+    static constexpr uint32_t HALF_ULP = 0x80000000u;
     __device__ static __forceinline__ void stg2_sr(__nv_bfloat16 *p, F2 v, uint32_t r)
     {
-        const uint32_t lo = __float_as_uint(v.x) + (r >> 16), hi = __float_as_uint(v.y) + (r & 0xffffu);
         uint32_t d;
-        asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.y), "f"(v.x), "r"(sr_fold(r)));
         *reinterpret_cast<uint32_t *>(p) = d;
     }
 };
@@ -659,6 +663,108 @@ stream_collide_x2_batch_kernel(const __grid_constant__ BatchArgs a)
         }
     }
     warp_end_x2<ST>(w, abort, a.error, a.work);
+}
+
+// Grid-wide barrier of a cooperative launch, with bounded waits.  Thread 0 of
+// every block arrives once, after all warps of the block are done; the last
+// arrival resets the arrival count and *reset (an item counter that the next
+// step but one uses), then releases the others by advancing the generation.
+// A wait longer than twice the bounded TMA wait raises the error flag and
+// gives up.  Returns false when the launch must stop (a wait gave up here, or
+// any warp raised the flag before arriving).  ctl[2] = arrivals, ctl[3] =
+// generation.
+__device__ __forceinline__ bool grid_barrier_bounded(unsigned int *ctl, unsigned int *reset, int *error)
+{
+    __shared__ int go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's stores before its arrival
+        const unsigned int g = *reinterpret_cast<volatile unsigned int *>(ctl + 3);
+        int ok = 1;
+        if (atomicAdd(ctl + 2, 1u) == gridDim.x - 1) {
+            atomicExch(ctl + 2, 0u);
+            atomicExch(reset, 0u);
+            __threadfence();
+            atomicAdd(ctl + 3, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer();
+            while (*reinterpret_cast<volatile unsigned int *>(ctl + 3) == g)
+                if (globaltimer() - t0 > 2 * WAIT_LIMIT_NS) {
+                    atomicExch(error, 1);
+                    ok = 0;
+                    break;
+                }
+        }
+        __threadfence();
+        go = ok && *reinterpret_cast<volatile int *>(error) == 0;
+    }
+    __syncthreads();
+    return go != 0;
+}
+
+// Persistent form of the batch kernel: steps k0 .. k0 + nsteps - 1 of a tick in
+// one cooperative launch (every block resident), a grid barrier between steps.
+// Each step hands out the items of the active domains (of one force variant)
+// from its own counter, ctl[k & 1]; a domain's arithmetic per step is that of
+// stream_collide_x2_batch_kernel, so the results are the same bit for bit.
+// After the barrier every thread orders the generic-proxy stores of the step
+// before the async-proxy (TMA) loads of the next.
+template <typename ST, int MODE, bool FORCED>
+__global__ void __launch_bounds__(THREADS, MIN_BLOCKS_BATCH_X2)
+stream_collide_x2_batch_persistent_kernel(const __grid_constant__ BatchArgs a, int k0, int nsteps)
+{
+    using T = Tile2<ST>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    WarpCtx w;
+    warp_begin_x2<ST>(w, smem);
+    unsigned int *ctl = a.ctl;
+    const int first = FORCED ? a.state->split_items : 0;
+    const int end = FORCED ? a.state->total_items : a.state->split_items;
+    const int n_active = a.state->n_active;
+    bool abort = false;
+    for (int k = k0; k < k0 + nsteps; ++k) {
+        const int parity = (a.parity + k) & 1;
+        unsigned int *work = ctl + (k & 1);
+        int last_slot = -1;
+        for (int item = abort ? end : first + next_item(w, work); item < end; item = first + next_item(w, work)) {
+            int lo = 0, hi = n_active;  // prefix[lo] <= item < prefix[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(a.prefix + mid) <= item) lo = mid;
+                else hi = mid;
+            }
+            const int slot = __ldg(a.active + lo);
+            const DomainDesc &D = a.domains[slot];
+            if (slot != last_slot) {
+                tensormap_acquire(&D.tload[parity]);
+                last_slot = slot;
+            }
+            const int local = item - __ldg(a.prefix + lo);
+            const StepParams &p = D.p;
+            const ST *fin = static_cast<const ST *>(D.f[parity]);
+            ST *fout = static_cast<ST *>(const_cast<void *>(D.f[parity ^ 1]));
+            const uint32_t step = __ldg(a.step0 + lo) + (uint32_t)k;
+            if (!run_item_x2<ST, MODE, FORCED>(w, p, &D.tload[parity], fin, fout, local % p.nstrips,
+                                               local / p.nstrips, step)) {
+                abort = true;
+                if (w.lane == 0) atomicExch(a.error, 1);
+                break;
+            }
+        }
+        if (!grid_barrier_bounded(ctl, ctl + ((k + 1) & 1), a.error)) {
+            abort = true;
+            break;
+        }
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    if (abort && w.lane == 0) {
+        // let this warp's copies in flight land before the shared memory goes away
+        for (int j = max(0, w.issued - T::NSLOT); j < w.issued; ++j) {
+            const uint32_t q = w.q_base + (uint32_t)j;
+            if (!mbar_wait_bounded(w.bars_u32 + 8 * (q % T::NSLOT), (q / T::NSLOT) & 1u)) break;
+        }
+    }
+    __syncwarp();
 }
 
 template <typename KernelFn>

@@ -3,8 +3,9 @@
 // Built once per (LBM_VARIANT_STORAGE, LBM_VARIANT_PART) by build.py: the
 // storage type selects the kernel family (packed two-cells-per-lane kernels for
 // FP32/FP16/BF16, the one-cell-per-lane kernel for FP64) and the part selects
-// which group of variants this object instantiates.  Every variant is
-// instantiated in exactly one part.
+// which group of variants this object instantiates (parts 0-3: step and batch
+// kernels; part 4, packed storages only: the persistent batch kernel).  Every
+// variant is instantiated in exactly one part.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -99,6 +100,21 @@ int batch_variant_blocks()
 {
     return occupancy_of(stream_collide_x2_batch_kernel<ST, MODE, FORCED>, Tile2<ST>::SMEM_BYTES);
 }
+
+template <typename ST, bool FORCED>
+cudaError_t batch_persistent_variant_launch(const BatchArgs &a, int k0, int nsteps, int grid, cudaStream_t s)
+{
+    void *args[] = {const_cast<BatchArgs *>(&a), &k0, &nsteps};
+    return cudaLaunchCooperativeKernel(
+        reinterpret_cast<const void *>(&stream_collide_x2_batch_persistent_kernel<ST, LBM_GI_FULL, FORCED>), grid,
+        THREADS, args, Tile2<ST>::SMEM_BYTES, s);
+}
+
+template <typename ST, bool FORCED>
+int batch_persistent_variant_blocks()
+{
+    return occupancy_of(stream_collide_x2_batch_persistent_kernel<ST, LBM_GI_FULL, FORCED>, Tile2<ST>::SMEM_BYTES);
+}
 #if LBM_VARIANT_STORAGE == 1
 using VST = __half;
 #elif LBM_VARIANT_STORAGE == 2
@@ -141,11 +157,17 @@ LBM_STEP_VARIANT(F_, true, true, true)
 #endif
 LBM_BATCH_VARIANT(U_, false)
 LBM_BATCH_VARIANT(U_, true)
-#else
+#elif LBM_VARIANT_PART == 3
 LBM_BATCH_VARIANT(C_, false)
 LBM_BATCH_VARIANT(C_, true)
 LBM_BATCH_VARIANT(F_, false)
 LBM_BATCH_VARIANT(F_, true)
+#elif LBM_VARIANT_STORAGE != 3
+// part 4 (packed storages only): the persistent batch kernel
+template cudaError_t batch_persistent_variant_launch<VST, false>(const BatchArgs &, int, int, int, cudaStream_t);
+template cudaError_t batch_persistent_variant_launch<VST, true>(const BatchArgs &, int, int, int, cudaStream_t);
+template int batch_persistent_variant_blocks<VST, false>();
+template int batch_persistent_variant_blocks<VST, true>();
 #endif
 
 }  // namespace lbm

@@ -27,4 +27,12 @@ cudaError_t batch_variant_launch(const BatchArgs &a, int grid, cudaStream_t s);
 template <typename ST, int MODE, bool FORCED>
 int batch_variant_blocks();
 
+// The persistent batch kernel (packed storages, full GI kernel): steps k0 ..
+// k0 + nsteps - 1 in one cooperative launch.
+template <typename ST, bool FORCED>
+cudaError_t batch_persistent_variant_launch(const BatchArgs &a, int k0, int nsteps, int grid, cudaStream_t s);
+
+template <typename ST, bool FORCED>
+int batch_persistent_variant_blocks();
+
 }  // namespace lbm

@@ -44,7 +44,8 @@ class Request(ctypes.Structure):
     """lbm_request: one steady solve submitted to a batch."""
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nu", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("U", ctypes.c_double), ("bnd", Boundaries), ("use_bnd", ctypes.c_int), ("fx", ctypes.c_double),
-                ("fy", ctypes.c_double), ("tol", ctypes.c_double), ("max_steps", ctypes.c_long)]
+                ("fy", ctypes.c_double), ("tol", ctypes.c_double), ("max_steps", ctypes.c_long),
+                ("check_every", ctypes.c_long)]
 
 
 class Result(ctypes.Structure):
@@ -53,7 +54,7 @@ class Result(ctypes.Structure):
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
-REQ_QUEUED, REQ_RUNNING, REQ_CONVERGED, REQ_NOT_CONVERGED, REQ_DIVERGED, REQ_FAILED = range(6)
+REQ_QUEUED, REQ_RUNNING, REQ_CONVERGED, REQ_NOT_CONVERGED, REQ_DIVERGED, REQ_FAILED, REQ_CANCELLED = range(7)
 
 
 class PopulationDesc(ctypes.Structure):
@@ -112,6 +113,7 @@ SIGNATURES = {
     "lbm_batch_poll": (ctypes.c_int, [_P, _L, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]),
     "lbm_batch_fields": (ctypes.c_int, [_P, _L, _P, _P, _P]),
     "lbm_batch_release": (ctypes.c_int, [_P, _L]),
+    "lbm_batch_cancel": (ctypes.c_int, [_P, _L]),
     "lbm_batch_run": (ctypes.c_int, [_P, _D]),
     "lbm_batch_start": (ctypes.c_int, [_P]),
     "lbm_batch_stop": (ctypes.c_int, [_P]),
@@ -366,7 +368,7 @@ class Batch:
         check(lib().lbm_batch_set_option(self._h, key.encode(), float(value)))
 
     def submit(self, nx, ny, nu, gamma, U=0.0, sides=None, solid=None, fx=0.0, fy=0.0, tol=1e-6,
-               max_steps=1_000_000) -> int:
+               max_steps=1_000_000, check_every=0) -> int:
         r = Request()
         r.nx, r.ny, r.nu, r.gamma, r.U = int(nx), int(ny), float(nu), float(gamma), float(U)
         keep = None
@@ -377,17 +379,18 @@ class Batch:
             r.bnd = b
             r.use_bnd = 1
         r.fx, r.fy, r.tol, r.max_steps = float(fx), float(fy), float(tol), int(max_steps)
+        r.check_every = int(check_every)
         rid = ctypes.c_long()
         check(lib().lbm_batch_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
         return rid.value
 
-    def submit_case(self, case, tol=1e-6, max_steps=1_000_000) -> int:
+    def submit_case(self, case, tol=1e-6, max_steps=1_000_000, check_every=0) -> int:
         """Submit a ``workloads.Case``; a batch starts every domain at rest and
         takes a uniform body force only."""
         if case.force_x is not None or case.rho0 is not None or case.ux0 is not None:
             raise ValueError("a batch request takes no force field and no initial fields")
         return self.submit(case.nx, case.ny, case.nu, case.gamma, case.U, case.sides, case.solid, case.Fx,
-                           case.Fy, tol, max_steps)
+                           case.Fy, tol, max_steps, check_every)
 
     def poll(self, rid: int):
         done = ctypes.c_int()
@@ -399,6 +402,9 @@ class Batch:
         out = [np.empty((ny, nx)) for _ in range(3)]
         check(lib().lbm_batch_fields(self._h, int(rid), *[_ptr(a) for a in out]))
         return tuple(out)
+
+    def cancel(self, rid: int):
+        check(lib().lbm_batch_cancel(self._h, int(rid)))
 
     def release(self, rid: int):
         check(lib().lbm_batch_release(self._h, int(rid)))

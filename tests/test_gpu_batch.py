@@ -86,11 +86,14 @@ def test_batch_domains_match_oracle(gi_mode):
 def test_batch_other_storages_match_oracle(storage, tol):
     """The mixed batch in FP64 storage (the one-cell batch kernel; FP64
     arithmetic, so tight) and in BF16 storage (8-bit mantissa deviations with
-    stochastic rounding, so loose): 100 steps, fields against the oracle."""
+    stochastic rounding, so loose): 100 steps, fields against the oracle (the
+    state itself: no window average of the velocity, which 16-bit batches take
+    by default)."""
     cases = mixed_cases()
     b = lbm.Batch(1 << 30, storage=storage)
     b.set_option("check_every", 50)
     b.set_option("rows_per_item", 8)
+    b.set_option("average_samples", 0)
     _, fields = run_fixed(b, cases, 100)
     for c, (rg, ug, vg) in zip(cases, fields):
         ro, uo, vo = oracle_at(c, 100)
@@ -295,3 +298,162 @@ def test_fields_and_release_from_two_threads():
         t.join()
         assert outcomes and all(outcomes), outcomes
         b.close()
+
+
+def _fixed_tile_batch(storage=lbm.STORAGE_F16, K=500):
+    b = lbm.Batch(1 << 30, storage=storage)
+    b.set_option("check_every", K)
+    b.set_option("rows_per_item", 8)  # no autotuning steps: check points follow the requests' own steps
+    return b
+
+
+def test_fp16_engine_staggered_admission_bitwise_equal_to_alone():
+    """Serving as continuous batching: FP16 requests submitted to the running
+    background engine at staggered times, while others run, each give exactly
+    the result (fields, steps, residual) of the same request run alone.  The
+    arithmetic of a domain, its stochastic-rounding bits (a hash of its own step
+    and cell), its velocity samples and its checks do not depend on the mix
+    (a fixed tile height keeps the autotuner's timing steps out)."""
+    cases = [wl.cavity(96, 300.0, 0.1, 0.6), wl.cavity(64, 150.0, 0.1, 0.9), wl.cavity(128, 500.0, 0.1, 0.5, ny=96),
+             wl.channel_obstacle(nx=192, ny=48, D=6, Re=20.0, U0=0.05, gamma=0.5, xc=48)]
+    alone = []
+    for c in cases:
+        b = _fixed_tile_batch()
+        rid = b.submit_case(c, tol=1e-3, max_steps=20000)
+        b.run()
+        done, res = b.poll(rid)
+        assert done
+        alone.append((res.state, res.steps, res.residual, b.fields(rid, c.nx, c.ny)))
+        b.close()
+    b = _fixed_tile_batch()
+    b.start()
+    ids = []
+    for c in cases:
+        ids.append(b.submit_case(c, tol=1e-3, max_steps=20000))
+        time.sleep(0.05)  # later requests join while earlier ones run
+    t_end = time.time() + 120
+    while time.time() < t_end and not all(b.poll(i)[0] for i in ids):
+        time.sleep(0.01)
+    b.stop()
+    for rid, c, (st, steps, r, f) in zip(ids, cases, alone):
+        done, res = b.poll(rid)
+        assert done and (res.state, res.steps) == (st, steps), (c.name, res.state, res.steps, st, steps)
+        assert res.residual == r
+        g = b.fields(rid, c.nx, c.ny)
+        for a, e in zip(g, f):
+            assert np.array_equal(a, e, equal_nan=True), c.name
+    b.close()
+
+
+def test_cancel_queued_and_running_requests_leaves_the_others_unchanged():
+    """lbm_batch_cancel: a queued request leaves the queue at once; a running
+    one stops between ticks (state CANCELLED, memory kept until release); the
+    requests that run on give results bitwise equal to a run without the
+    cancelled ones."""
+    keep = [wl.cavity(96, 200.0, 0.1, 0.7), wl.cavity(64, 300.0, 0.1, 0.5)]
+    drop_running, drop_queued = wl.cavity(128, 400.0, 0.1, 0.4), wl.cavity(160, 100.0, 0.1, 0.8)
+
+    ref = _fixed_tile_batch()
+    rids = [ref.submit_case(c, tol=1e-300, max_steps=3000) for c in keep]
+    ref.run()
+    expect = [ref.fields(r, c.nx, c.ny) for r, c in zip(rids, keep)]
+    ref.close()
+
+    one = 2 * 9 * 128 * 128 * 2 + 4 * 128 * 128 * 8  # room for the three smaller domains, not the fourth
+    b = lbm.Batch(3 * one, storage=lbm.STORAGE_F16)
+    b.set_option("check_every", 500)
+    b.set_option("rows_per_item", 8)
+    ids = [b.submit_case(c, tol=1e-300, max_steps=3000) for c in keep]
+    r_run = b.submit_case(drop_running, tol=1e-300, max_steps=3000)
+    r_q = b.submit_case(drop_queued, tol=1e-300, max_steps=3000)
+    assert b.stats()["queued"] == 4
+    b.cancel(r_q)
+    done, res = b.poll(r_q)
+    assert done and res.state == lbm.REQ_CANCELLED and res.steps == 0
+    b.start()
+    t_end = time.time() + 30
+    while time.time() < t_end and b.poll(r_run)[1].state == lbm.REQ_QUEUED:
+        time.sleep(0.001)
+    b.cancel(r_run)
+    while time.time() < t_end and not all(b.poll(i)[0] for i in ids + [r_run]):
+        time.sleep(0.01)
+    b.stop()
+    done, res = b.poll(r_run)
+    assert done and res.state == lbm.REQ_CANCELLED and 0 <= res.steps < 3000
+    with pytest.raises(lbm.LbmError):
+        b.cancel(r_run)  # finished
+    for rid, c, e in zip(ids, keep, expect):
+        done, res = b.poll(rid)
+        assert done and res.state == lbm.REQ_NOT_CONVERGED and res.steps == 3000
+        for a, x in zip(b.fields(rid, c.nx, c.ny), e):
+            assert np.array_equal(a, x, equal_nan=True), c.name
+    for rid in ids + [r_run, r_q]:
+        b.release(rid)
+    assert b.stats()["device_bytes"] == 0
+    b.close()
+
+
+def test_fp16_window_average_reduces_the_steady_error():
+    """The 128 x 128 cavity (Re = 100, gamma = 0.5) in FP16 to r < 1e-3 with
+    checks 1000 steps apart, with the default 16 velocity samples per check
+    window and without: against the oracle's steady state the averaged result is
+    closer (stochastic rounding noise removed) and within 6e-4."""
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "cavity128_re100_g05_steady.npz"))
+    uo, vo = gold["ux"].astype(np.float64), gold["uy"].astype(np.float64)
+    c = wl.cavity(128, 100.0, 0.1, 0.5)
+    err = {}
+    for m in (0, 16):
+        b = lbm.Batch(1 << 30, storage=lbm.STORAGE_F16)
+        b.set_option("check_every", 1000)
+        b.set_option("average_samples", m)
+        rid = b.submit_case(c, tol=1e-3, max_steps=200000)
+        b.run()
+        done, res = b.poll(rid)
+        assert done and res.state == lbm.REQ_CONVERGED
+        _, u, v = b.fields(rid, c.nx, c.ny)
+        err[m] = np.sqrt(((u - uo) ** 2 + (v - vo) ** 2).sum() / (uo ** 2 + vo ** 2).sum())
+        b.close()
+    print("FP16 128^2 steady L2 vs oracle: single state", err[0], "window average", err[16])
+    assert err[16] < 0.8 * err[0] and err[16] < 6e-4, err
+
+
+@pytest.mark.parametrize("storage", [lbm.STORAGE_F16, lbm.STORAGE_F32])
+def test_persistent_kernel_bitwise_equal_to_per_step_launches(storage):
+    """The persistent batch kernel (every step of a tick's segment in one
+    cooperative launch, a bounded grid barrier between steps) against a launch
+    per step: the same fields bit for bit, for a set of unforced cavities and
+    for a set of forced channels (one force variant each), through ticks with
+    window samples and domains of different sizes and rows."""
+    cavities = [wl.cavity(96, 300.0, 0.1, 0.6), wl.cavity(64, 150.0, 0.1, 0.9),
+                wl.cavity(200, 500.0, 0.1, 0.5, ny=70), wl.cavity(33, 50.0, 0.1, 1.0)]
+    channels = [wl.poiseuille(100, 33, 0.05, 0.7, 2e-6),
+                wl.channel_obstacle(nx=160, ny=48, D=8, Re=20.0, U0=0.05, gamma=0.4, xc=40)]
+    for cases in (cavities, channels):
+        out = {}
+        for mode in (0, 1):
+            b = lbm.Batch(1 << 30, storage=storage)
+            b.set_option("check_every", 200)
+            b.set_option("rows_per_item", 8)
+            b.set_option("persistent", mode)
+            _, out[mode] = run_fixed(b, cases, 1000)
+            b.close()
+        for c, f0, f1 in zip(cases, out[0], out[1]):
+            for a0, a1 in zip(f0, f1):
+                assert np.array_equal(a0, a1, equal_nan=True), (c.name, storage)
+
+
+def test_persistent_option_with_mixed_force_variants_runs_per_step():
+    """A batch holding forced and unforced domains cannot use the one-variant
+    persistent kernel: with the option on it runs per-step launches, and the
+    domains still match the oracle."""
+    cases = mixed_cases()
+    b = lbm.Batch(1 << 30, storage=lbm.STORAGE_F32)
+    b.set_option("check_every", 50)
+    b.set_option("rows_per_item", 8)
+    b.set_option("persistent", 1)
+    _, fields = run_fixed(b, cases, 100)
+    for c, (rg, ug, vg) in zip(cases, fields):
+        ro, uo, vo = oracle_at(c, 100)
+        m = fluid(c)
+        assert max(np.abs(ug - uo)[m].max(), np.abs(vg - vo)[m].max()) < 2e-6, c.name
+    b.close()
