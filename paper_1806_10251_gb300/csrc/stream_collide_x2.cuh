@@ -38,11 +38,24 @@ struct Tile2 {
 };
 
 // Resident blocks per SM the register budget is sized for: four (16 warps) for
-// the unforced single-domain kernel; three for the forced one (the source
-// terms) and for the batch kernel, whose per-domain parameters live in global
-// memory and hold more registers.
+// the unforced kernels; three for the forced ones (the source terms).  The
+// batch kernels read a domain's parameters from a per-warp copy in shared
+// memory (see copy_params): through global memory they held about 40 more
+// registers and forced three blocks per SM.
 constexpr int MIN_BLOCKS_X2 = 4;
 constexpr int MIN_BLOCKS_BATCH_X2 = 3;
+
+// Copy a domain's parameters into the warp's shared-memory slot (when the
+// warp's item moves to another domain), so that the step reads them like the
+// single-domain kernel reads its launch parameters.
+__device__ __forceinline__ void copy_params(StepParams &dst, const StepParams &src, int lane)
+{
+    static_assert(sizeof(StepParams) % 4 == 0, "word copy");
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
+    for (int i = lane; i < (int)(sizeof(StepParams) / 4); i += 32) d[i] = s[i];
+    __syncwarp();
+}
 
 // Pairs of stored values <-> F2 (storage scale and rounding as StorageTraits).
 template <typename ST> struct PairIO;
@@ -625,10 +638,12 @@ stream_collide_x2_kernel(const __grid_constant__ StepParams p, const __grid_cons
 // the prefix sums.  A domain's arithmetic does not depend on which other
 // domains share the launch.
 template <typename ST, int MODE, bool FORCED>
-__global__ void __launch_bounds__(THREADS, MIN_BLOCKS_BATCH_X2)
+__global__ void __launch_bounds__(THREADS, FORCED ? MIN_BLOCKS_BATCH_X2 : MIN_BLOCKS_X2)
 stream_collide_x2_batch_kernel(const __grid_constant__ BatchArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ StepParams sp[WARPS];
+    StepParams &p = sp[threadIdx.x >> 5];
     WarpCtx w;
     warp_begin_x2<ST>(w, smem);
     bool abort = false;
@@ -649,10 +664,10 @@ stream_collide_x2_batch_kernel(const __grid_constant__ BatchArgs a)
             // the descriptor was written by a host copy into global memory:
             // acquire it for the tensor-map proxy before the first TMA use
             tensormap_acquire(&D.tload[a.parity]);
+            copy_params(p, D.p, w.lane);
             last_slot = slot;
         }
         const int local = item - __ldg(a.prefix + lo);
-        const StepParams &p = D.p;
         const ST *fin = static_cast<const ST *>(D.f[a.parity]);
         ST *fout = static_cast<ST *>(const_cast<void *>(D.f[a.parity ^ 1]));
         const uint32_t step = __ldg(a.step0 + lo) + (uint32_t)a.k;
@@ -710,11 +725,13 @@ __device__ __forceinline__ bool grid_barrier_bounded(unsigned int *ctl, unsigned
 // After the barrier every thread orders the generic-proxy stores of the step
 // before the async-proxy (TMA) loads of the next.
 template <typename ST, int MODE, bool FORCED>
-__global__ void __launch_bounds__(THREADS, MIN_BLOCKS_BATCH_X2)
+__global__ void __launch_bounds__(THREADS, FORCED ? MIN_BLOCKS_BATCH_X2 : MIN_BLOCKS_X2)
 stream_collide_x2_batch_persistent_kernel(const __grid_constant__ BatchArgs a, int k0, int nsteps)
 {
     using T = Tile2<ST>;
     extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ StepParams sp[WARPS];
+    StepParams &p = sp[threadIdx.x >> 5];
     WarpCtx w;
     warp_begin_x2<ST>(w, smem);
     unsigned int *ctl = a.ctl;
@@ -737,10 +754,10 @@ stream_collide_x2_batch_persistent_kernel(const __grid_constant__ BatchArgs a, i
             const DomainDesc &D = a.domains[slot];
             if (slot != last_slot) {
                 tensormap_acquire(&D.tload[parity]);
+                copy_params(p, D.p, w.lane);
                 last_slot = slot;
             }
             const int local = item - __ldg(a.prefix + lo);
-            const StepParams &p = D.p;
             const ST *fin = static_cast<const ST *>(D.f[parity]);
             ST *fout = static_cast<ST *>(const_cast<void *>(D.f[parity ^ 1]));
             const uint32_t step = __ldg(a.step0 + lo) + (uint32_t)k;
