@@ -11,14 +11,20 @@ data-parallel over independent domains; no collective on the data path), so
 scaling is weak.  Inputs (1.2 GB of populations per replica) exceed the 129 MB
 L2, so no L2 flush is needed between steps.
 
+The default line also carries "batch": the batch study (steady solves/s of
+the FP16 batch against the plain FP32 solver one domain at a time) on the first
+--batch-domains cavities of the seeded 256-cavity set, with the FP16 results'
+error against the oracle's stored steady states.
+
 --impl reference times the FP64 CPU oracle on the host cores instead.
 
-Other workloads (--workload, each prints its own JSON line): batch (steady
-solves/s of the seeded cavity set, FP16 batch against the plain FP32 solver one
-domain at a time), serve (a Poisson stream of steady-solve requests into the
-batch engine: latency percentiles, aggregate MLUPS), precision (storage formats
-to steady state on a scaled obstacle channel, against FP64 storage), gamma
-(steps to steady state per preconditioning parameter).
+Other workloads (--workload, each prints its own JSON line): batch (the batch
+study on --batch-count domains, with FP64-storage GPU references across the
+sizes), serve (a Poisson stream of steady-solve requests into the batch engine:
+latency percentiles per request kind, aggregate MLUPS), precision (storage
+formats to steady state on a scaled obstacle channel, against FP64 storage),
+gamma (steps to steady state per preconditioning parameter), cylinder (wake
+length and drag of the square cylinder in a channel, Re 5-60).
 """
 from __future__ import annotations
 
@@ -67,7 +73,7 @@ def parse():
     ap.add_argument("--e2e-check-every", type=int, default=100)
     ap.add_argument("--cells-per-item", type=int, default=0,
                     help="rows per work item of the step kernel (0 = automatic)")
-    ap.add_argument("--workload", choices=["cavity", "batch", "serve", "precision", "gamma"], default="cavity",
+    ap.add_argument("--workload", choices=["cavity", "batch", "serve", "precision", "gamma", "cylinder"], default="cavity",
                     help="cavity: the timed step of one large domain (default); batch: steady solves/s of "
                          "independent cavities, FP16 batch against the plain FP32 solver one domain at a time; "
                          "serve: a Poisson stream of steady-solve requests into the batch engine")
@@ -82,6 +88,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=2.0, help="serve: mean arrivals per second")
     ap.add_argument("--request-max-steps", type=int, default=100000,
                     help="serve: steps after which a request is returned as not converged")
+    ap.add_argument("--cyl-d", type=int, default=16, help="cylinder: side of the square cylinder in cells")
+    ap.add_argument("--serve-wall-s", type=float, default=600.0,
+                    help="serve: the session ends this long after the first arrival (what is left is cancelled)")
     ap.add_argument("--side-min", type=int, default=128)
     ap.add_argument("--side-max", type=int, default=512)
     ap.add_argument("--scale", type=int, default=16,
@@ -385,8 +394,13 @@ def run_serve(args, rank):
     channel, p = 1/2; side on multiples of 32 in [side-min, side-max]; Re ~
     U[50, 1000]; gamma ~ U[0.2, 1.0]; FP16 storage) submitted at their arrival
     times to the batch engine running on a background thread (continuous
-    batching: admission by device footprint as memory frees up).  Reports the
-    arrival-to-steady latency percentiles, the aggregate MLUPS and the queue."""
+    batching: admission by device footprint as memory frees up).  Each request
+    carries a step cap and the check interval of the batch study
+    (check_interval); the session ends --serve-wall-s after the first arrival,
+    cancelling what is still queued or running then.  Reports converged / not
+    converged / diverged / cancelled counts per kind, the arrival-to-done
+    latency percentiles of all requests and of the converged ones, queue waits,
+    the aggregate MLUPS and the queue depth."""
     import numpy as np
     import torch
 
@@ -402,52 +416,128 @@ def run_serve(args, rank):
     b.set_option("check_every", args.check_every)
     b.start()
     t0 = time.perf_counter()
-    ids, pending, done = [], set(), {}
+    ids, kinds, pending, done = [], {}, set(), {}
     depth = []
-    for ta, c in reqs:
-        while True:
-            now = time.perf_counter() - t0
-            if now >= ta:
-                break
-            for rid in list(pending):
-                fin, res = b.poll(rid)
-                if fin:
-                    done[rid] = res
-                    pending.discard(rid)
-                    b.release(rid)
-            time.sleep(min(0.002, ta - now))
-        rid = b.submit_case(c, tol=args.tol, max_steps=args.request_max_steps)
-        ids.append(rid)
-        pending.add(rid)
-        st = b.stats()
-        depth.append((st["running"], st["queued"]))
-    while pending:
+
+    def harvest():
         for rid in list(pending):
             fin, res = b.poll(rid)
             if fin:
                 done[rid] = res
                 pending.discard(rid)
                 b.release(rid)
+
+    for ta, c in reqs:
+        while True:
+            now = time.perf_counter() - t0
+            if now >= ta:
+                break
+            harvest()
+            time.sleep(min(0.002, ta - now))
+        rid = b.submit_case(c, tol=args.tol, max_steps=args.request_max_steps,
+                            check_every=check_interval(c, args.check_every))
+        ids.append(rid)
+        kinds[rid] = "cavity" if c.name.startswith("cavity") else "channel"
+        pending.add(rid)
+        st = b.stats()
+        depth.append((st["running"], st["queued"]))
+    cancelled_at = None
+    while pending:
+        harvest()
+        if cancelled_at is None and time.perf_counter() - t0 > args.serve_wall_s:
+            cancelled_at = time.perf_counter() - t0
+            for rid in list(pending):
+                try:
+                    b.cancel(rid)
+                except lbm.LbmError:
+                    pass  # finished meanwhile
         time.sleep(0.002)
     wall = time.perf_counter() - t0
     stats = b.stats()
     b.stop()
     b.close()
-    lat = np.array([done[i].t_done - done[i].t_submit for i in ids])
-    queue = np.array([done[i].t_admit - done[i].t_submit for i in ids])
+    names = {lbm.REQ_CONVERGED: "converged", lbm.REQ_NOT_CONVERGED: "not_converged",
+             lbm.REQ_DIVERGED: "diverged", lbm.REQ_CANCELLED: "cancelled", lbm.REQ_FAILED: "failed"}
+
+    def pct(x):
+        x = np.asarray(x)
+        return ({"p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99)), "n": int(x.size)}
+                if x.size else {"n": 0})
+
+    lat = {i: done[i].t_done - done[i].t_submit for i in ids}
+    per_kind = {}
+    for kind in ("cavity", "channel"):
+        mine = [i for i in ids if kinds[i] == kind]
+        counts = {v: 0 for v in names.values()}
+        for i in mine:
+            counts[names.get(done[i].state, "failed")] += 1
+        per_kind[kind] = {"requests": len(mine), **counts,
+                          "latency_converged_s": pct([lat[i] for i in mine if done[i].state == lbm.REQ_CONVERGED])}
+    queue = [done[i].t_admit - done[i].t_submit for i in ids if done[i].t_admit > 0]
+    conv = [lat[i] for i in ids if done[i].state == lbm.REQ_CONVERGED]
     line = {"metric": "arrival-to-steady latency and aggregate MLUPS (serving, FP16 batch engine)",
-            "workload": "serve", "value": float(np.percentile(lat, 50)), "unit": "s (p50 latency)",
+            "workload": "serve", "value": pct(conv).get("p50"), "unit": "s (p50 latency of converged requests)",
             "higher_is_better": False,
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "mean": float(lat.mean()), "max": float(lat.max())},
-            "queue_wait_s": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+            "latency_all_s": pct(list(lat.values())), "latency_converged_s": pct(conv),
+            "queue_wait_s": pct(queue), "per_kind": per_kind,
             "aggregate_mlups": stats["cell_updates"] / wall / 1e6, "wall_s": wall,
+            "cancelled_at_s": cancelled_at,
             "max_running": int(max(d[0] for d in depth)), "max_queued": int(max(d[1] for d in depth)),
-            "converged": int(sum(done[i].state == lbm.REQ_CONVERGED for i in ids)), "requests": len(ids),
+            "requests": len(ids),
             "config": {"rate_per_s": args.rate, "requests": args.requests, "side": [args.side_min, args.side_max],
-                       "request_max_steps": args.request_max_steps,
-                       "tol": args.tol, "check_every": args.check_every, "budget_bytes": budget,
+                       "request_max_steps": args.request_max_steps, "session_wall_s": args.serve_wall_s,
+                       "tol": args.tol, "check_every": args.check_every,
+                       "check_rule": "per request: check_interval (8 transits)", "budget_bytes": budget,
                        "stream": "poisson_requests(seed=0)"},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cylinder(args, rank):
+    """Flow past the square cylinder in a channel (Sec. 6: 50 D x 8 D, cylinder
+    at 12.5 D, parabolic inflow of peak U = 0.1, convective outflow, gamma =
+    0.5): for each Reynolds number (U D / nu) the steady field (FP32, r < 2e-7
+    between checks 1000 steps apart), the recirculation length behind the rear
+    face on the channel axis against the printed correlation L_r / D = -0.065 +
+    0.0554 Re (5 < Re < 60), and the drag coefficient from the momentum
+    exchange, C_D = 2 gamma F_x / (rho0 U^2 D) (the preconditioned momentum
+    equation divides every flux by gamma)."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1806_10251_gb300 import lbm
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    rows = []
+    for Re in (5.0, 10.0, 20.0, 30.0, 40.0, 50.0, 60.0):
+        c = wl.square_cylinder(args.cyl_d, Re, 0.1, 0.5)
+        g = lbm.solver_from_case(c)
+        t = time.perf_counter()
+        st, steps, r = g.run_to_steady(2e-7, 1000, 3_000_000, raise_on_error=False)
+        sec = time.perf_counter() - t
+        _, u, _ = g.fields()
+        F = g.drag()
+        m = c.meta
+        ya = int(m["y_axis"])
+        ax = 0.5 * (u[ya, :] + u[ya + 1, :])
+        k = int(np.ceil(m["x_rear"]))
+        Lr = 0.0
+        if ax[k] < 0:
+            while k < c.nx - 1 and not (ax[k] < 0 <= ax[k + 1]):
+                k += 1
+            Lr = (k + (-ax[k]) / (ax[k + 1] - ax[k]) - m["x_rear"]) / m["D"]
+        g.close()
+        rows.append({"Re": Re, "Lr_over_D": Lr, "correlation": -0.065 + 0.0554 * Re,
+                     "C_D": 2 * c.gamma * F[0] / (0.1 ** 2 * m["D"]), "C_L": 2 * c.gamma * F[1] / (0.1 ** 2 * m["D"]),
+                     "steps": steps, "residual": r, "status": st, "seconds": sec})
+    line = {"metric": "square-cylinder wake length and drag (Sec. 6)", "workload": "cylinder",
+            "value": float(np.mean([abs(x["Lr_over_D"] / x["correlation"] - 1) for x in rows if x["Re"] >= 10])),
+            "unit": "mean relative deviation of L_r/D from the correlation (Re 10-60)", "higher_is_better": False,
+            "rows": rows, "config": {"D": args.cyl_d, "U": 0.1, "gamma": 0.5, "storage": "f32", "gi_mode": "full",
+                                     "channel": "50 D x 8 D, cylinder at 12.5 D"},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
@@ -582,6 +672,8 @@ def main():
         return run_precision(args, rank)
     if args.workload == "gamma":
         return run_gamma(args, rank)
+    if args.workload == "cylinder":
+        return run_cylinder(args, rank)
 
     import numpy as np
     import torch

@@ -19,6 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_gb300.so")
+# debug build: every computed kernel index checked (LBM_DEBUG_BOUNDS=1)
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_BUILD, "liblbm_gb300_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE]
@@ -43,27 +46,32 @@ def _headers():
                   + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in sources() + _headers() + [__file__])
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Build the library (debug=True: the bounds-checking variant, into its own
+    folder) and return its path."""
+    out_dir, lib_path = (DEBUG_BUILD, DEBUG_LIB) if debug else (BUILD, LIB)
+    if debug:
+        extra_flags = (*extra_flags, "-DLBM_DEBUG_BOUNDS=1")
+    if not force and up_to_date(lib_path):
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     jobs = []  # (source, object, defines)
     for src in sources():
         stem = os.path.basename(src)[:-3]
         if stem == "variants":
             for st, part in VARIANT_MATRIX:
-                jobs.append((src, os.path.join(BUILD, f"variants_s{st}_p{part}.o"),
+                jobs.append((src, os.path.join(out_dir, f"variants_s{st}_p{part}.o"),
                              [f"-DLBM_VARIANT_STORAGE={st}", f"-DLBM_VARIANT_PART={part}"]))
         else:
-            jobs.append((src, os.path.join(BUILD, stem + ".o"), []))
+            jobs.append((src, os.path.join(out_dir, stem + ".o"), []))
     # the largest units first, so that the small ones fill in around them
     jobs.sort(key=lambda j: os.path.basename(j[0]) != "variants.cu")
     objs = [j[1] for j in jobs]
@@ -80,11 +88,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 1, len(jobs)))) as ex:
         list(ex.map(compile_one, jobs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib_path + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

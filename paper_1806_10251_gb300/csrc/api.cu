@@ -236,6 +236,7 @@ lbm_status check_device_error(lbm_ctx *c)
         cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
         cudaMemsetAsync(c->d_work, 0, 2 * sizeof(unsigned int), c->stream);
         cudaStreamSynchronize(c->stream);
+        if (v == 2) return fail(LBM_ERR_CUDA, "debug bounds check: a kernel index was out of range (device error flag 2)");
         return fail(LBM_ERR_CUDA, "a kernel's bounded wait expired (device error flag raised)");
     }
     return LBM_OK;

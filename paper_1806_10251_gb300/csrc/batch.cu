@@ -683,6 +683,7 @@ lbm_status tick(lbm_batch *b, bool *busy)
         cudaMemsetAsync(b->d_work, 0, 2 * sizeof(unsigned int), b->stream);
         cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), b->stream);
         cudaStreamSynchronize(b->stream);
+        if (err == 2) return bfail(LBM_ERR_CUDA, "debug bounds check: a batched kernel index was out of range");
         return bfail(LBM_ERR_CUDA, "a batched step kernel's bounded wait expired");
     }
     const double t = seconds(b);

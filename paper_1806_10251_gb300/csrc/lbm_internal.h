@@ -9,7 +9,27 @@
 
 #include "../../include/lbm.h"
 
+// Debug build (compiled with LBM_DEBUG_BOUNDS=1: build(debug=True)): the step
+// kernels check every computed index of their global-memory accesses (and the
+// general pull's ring columns) against the buffer it addresses; a violation
+// sets the device error flag to 2 and skips the access, and the host reports
+// it at the next synchronising call.
+#ifndef LBM_DEBUG_BOUNDS
+#define LBM_DEBUG_BOUNDS 0
+#endif
+#define LBM_IN_BOUNDS(idx, extent, err) \
+    (!LBM_DEBUG_BOUNDS || ::lbm::debug_in_bounds((long long)(idx), (long long)(extent), (err)))
+
 namespace lbm {
+
+#ifdef __CUDACC__
+__device__ __forceinline__ bool debug_in_bounds(long long i, long long n, int *err)
+{
+    if (i >= 0 && i < n) return true;
+    if (err) atomicExch(err, 2);
+    return false;
+}
+#endif
 
 // Columns of one warp strip of the stream-collide kernel (one per lane), warps
 // per block.

@@ -34,7 +34,8 @@ __device__ __forceinline__ R boundary_value(const StepParams &p, const Consts<R>
     const int side = outx ? (sx < 0 ? 0 : 1) : (sy < 0 ? 2 : 3);
     if (side == 1 && p.outlet) {
         const int gy = !p.pery ? sy : (sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy));
-        return static_cast<const R *>(p.ghost_in)[(2 + ghost_slot(a)) * p.ny + gy];
+        const long long gi = (long long)(2 + ghost_slot(a)) * p.ny + gy;
+        return LBM_IN_BOUNDS(gi, 5LL * p.ny, p.error) ? static_cast<const R *>(p.ghost_in)[gi] : own_opp;
     }
     const R wa = a == 0 ? R(4.0 / 9.0) : (a <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
     R uw = c.wall6[side][0];
@@ -105,6 +106,7 @@ template <typename R>
 __device__ __forceinline__ void outlet_update(const StepParams &p, const Consts<R> &c, int y, const R (&g)[9], R Fx,
                                               R Fy)
 {
+    if (!LBM_IN_BOUNDS(y, p.ny, p.error)) return;
     R drho, ux, uy;
     cell_state(c, g, Fx, Fy, drho, ux, uy);
     const R *gin = static_cast<const R *>(p.ghost_in);

@@ -246,8 +246,9 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
                         const int xd = side == 0 ? j - 2 : p.nx + j;
                         const int xs = side == 0 ? p.nx - 2 + j : j;
                         const int cd = xd - x0 + T::PAD;
-                        if (cd >= 0 && cd < T::BWX)
-                            dst[a * T::BWX + cd] = fin[(size_t)a * (size_t)p.plane + (size_t)s * p.pitch + xs];
+                        const long long fi = (long long)a * p.plane + (long long)s * p.pitch + xs;
+                        if (cd >= 0 && cd < T::BWX && LBM_IN_BOUNDS(fi, 9 * p.plane, p.error))
+                            dst[a * T::BWX + cd] = fin[fi];
                     }
                 }
                 __syncwarp();
@@ -268,8 +269,10 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
                 bool inside = !outx && !outy;
                 if (inside && has_solid) {
                     const int wx = p.perx ? wrap(sx, p.nx) : sx, wy = p.pery ? wrap(sy, p.ny) : sy;
-                    inside = __ldg(p.solid + (size_t)wy * p.pitch + wx) == 0;
+                    const long long si = (long long)wy * p.pitch + wx;
+                    inside = LBM_IN_BOUNDS(si, p.plane, p.error) && __ldg(p.solid + si) == 0;
                 }
+                if (inside && !LBM_IN_BOUNDS(cc - ex, T::BWX, p.error)) inside = false;
                 if (inside) {
                     g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + cc - ex]);
                 } else if (outx || outy) {
@@ -292,7 +295,8 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
             const bool in_x = (xc >= 0 && xc < p.nx) || (p.perx && (xc == -1 || xc == p.nx));
             if (row_in && in_x) {
                 const int xw = wrap(xc, p.nx);
-                if (!has_solid || __ldg(p.solid + (size_t)rw * p.pitch + xw) == 0) {
+                const long long si = (long long)rw * p.pitch + xw;
+                if (!has_solid || (LBM_IN_BOUNDS(si, p.plane, p.error) && __ldg(p.solid + si) == 0)) {
                     pull_general(xc, r, g);
                     R s = g[0];
 #pragma unroll
@@ -489,8 +493,10 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
                 Fy = c.Fy;
                 if (p.force) {
                     const size_t i = (size_t)y * p.pitch + min(x, p.nx - 1);
-                    Fx = R(__ldg(p.force + i));
-                    Fy = R(__ldg(p.force + (size_t)p.plane + i));
+                    if (LBM_IN_BOUNDS(i, p.plane, p.error)) {
+                        Fx = R(__ldg(p.force + i));
+                        Fy = R(__ldg(p.force + (size_t)p.plane + i));
+                    }
                 }
             }
             R out[9];

@@ -261,8 +261,9 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
                     const int xd = side == 0 ? j - 2 : p.nx + j;
                     const int xs = side == 0 ? p.nx - 2 + j : j;
                     const int cd = xd - x0 + T::PAD;
-                    if (cd >= 0 && cd < T::BWX)
-                        dst[a * T::BWX + cd] = fin[(size_t)a * (size_t)p.plane + (size_t)s * p.pitch + xs];
+                    const long long fi = (long long)a * p.plane + (long long)s * p.pitch + xs;
+                    if (cd >= 0 && cd < T::BWX && LBM_IN_BOUNDS(fi, 9 * p.plane, p.error))
+                        dst[a * T::BWX + cd] = fin[fi];
                 }
             }
             __syncwarp();
@@ -283,8 +284,10 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
             bool inside = !outx && !outy;
             if (inside && has_solid) {
                 const int wx = p.perx ? wrap(sx, p.nx) : sx, wy = p.pery ? wrap(sy, p.ny) : sy;
-                inside = __ldg(p.solid + (size_t)wy * p.pitch + wx) == 0;
+                const long long si = (long long)wy * p.pitch + wx;
+                inside = LBM_IN_BOUNDS(si, p.plane, p.error) && __ldg(p.solid + si) == 0;
             }
+            if (inside && !LBM_IN_BOUNDS(ck - ex, T::BWX, p.error)) inside = false;
             if (inside) g[a] = StorageTraits<ST>::cvt(src[a * T::BWX + ck - ex]);
             else if (outx || outy)
                 g[a] = boundary_value<R>(p, c, a, ex, ey, sx, sy, outx, outy,
@@ -303,7 +306,8 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
         const bool in_x = (xc >= 0 && xc < p.nx) || (p.perx && (xc == -1 || xc == p.nx));
         if (row_in && in_x) {
             const int xw = wrap(xc, p.nx);
-            if (!has_solid || __ldg(p.solid + (size_t)rw * p.pitch + xw) == 0) {
+            const long long si = (long long)rw * p.pitch + xw;
+            if (!has_solid || (LBM_IN_BOUNDS(si, p.plane, p.error) && __ldg(p.solid + si) == 0)) {
                 pull_general(xc, r, g);
                 R s = g[0];
 #pragma unroll
@@ -517,10 +521,12 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
                 Fy = ld(p.c2.Fy);
                 if (p.force) {
                     const size_t i = (size_t)y * p.pitch + xe;
-                    const float2 fx2 = __ldg(reinterpret_cast<const float2 *>(p.force + i));
-                    const float2 fy2 = __ldg(reinterpret_cast<const float2 *>(p.force + plane + i));
-                    Fx = f2(fx2.x, fx2.y);
-                    Fy = f2(fy2.x, fy2.y);
+                    if (LBM_IN_BOUNDS(i + 1, plane, p.error)) {
+                        const float2 fx2 = __ldg(reinterpret_cast<const float2 *>(p.force + i));
+                        const float2 fy2 = __ldg(reinterpret_cast<const float2 *>(p.force + plane + i));
+                        Fx = f2(fx2.x, fx2.y);
+                        Fy = f2(fy2.x, fy2.y);
+                    }
                 }
             }
             F2 out[9];
@@ -560,7 +566,9 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
             // 2-wide stores of the row (x0 + SW <= pitch: the odd cell past nx, if
             // any, lands in the row padding)
             ST *fo = fout + (size_t)y * p.pitch + xe;
-            if constexpr (StorageTraits<ST>::kReduced) {
+            if (!LBM_IN_BOUNDS((long long)y * p.pitch + xe + 1, p.plane, p.error)) {
+                // debug build: a row index outside the buffer skips the stores
+            } else if constexpr (StorageTraits<ST>::kReduced) {
                 // one store path for both rounding modes (no cold alternative in the loop)
                 const uint32_t h = mix32(seed ^ (uint32_t)(y * p.nx + xe));  // one hash per pair of cells
 #pragma unroll

@@ -122,8 +122,13 @@ SIGNATURES = {
 }
 
 
+def debug_bounds() -> bool:
+    """LBM_DEBUG_BOUNDS=1 in the environment selects the bounds-checking build."""
+    return os.environ.get("LBM_DEBUG_BOUNDS", "0") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.DEBUG_LIB if debug_bounds() else _build.LIB
 
 
 def lib() -> ctypes.CDLL:
@@ -131,7 +136,7 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(debug=debug_bounds())
             L = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(L, name)

@@ -349,6 +349,47 @@ def test_full_size_4096_cavity_sampled_windows(gamma):
     assert np.isfinite(ug).all()
 
 
+def test_full_size_4096_cavity_fp16_windows_round_to_a_neighbour():
+    """The FP16 bench case (4096 x 4096 cavity, Re = 1000, gamma = 0.5, FP16
+    storage of 2^14 g with stochastic rounding) in the bench's launch
+    configuration: after 300 steps, on sampled windows (corners, lid, walls,
+    seams, interior), every stored value of the GPU's step n lies within one
+    FP16 spacing of the oracle's FP64 step taken from the GPU's step n - 1 (the
+    rounding picks one of the two neighbouring FP16 values; FP32 collision
+    arithmetic adds far less), and the signed errors average to about zero
+    (stochastic rounding is unbiased)."""
+    c = wl.cavity(4096, 1000.0, 0.1, 0.5)
+    g = lbm.solver_from_case(c, storage=lbm.STORAGE_F16)
+    g.step(299)
+    fprev = g.populations()
+    g.step(1)
+    fnext = g.populations()
+    n = 4096
+    windows = [(0, 0), (n - 12, 0), (0, n - 12), (n - 12, n - 12), (2040, n - 12), (0, 2000),
+               (n - 12, 3000), (1500, 0), (120, 50), (250, 1777), (2047, 2047), (127, 53)]
+    W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    excess, signed = 0.0, []
+    for (x0, y0) in windows:
+        xa, xb = max(x0 - 2, 0), min(x0 + 14, n)
+        ya, yb = max(y0 - 2, 0), min(y0 + 14, n)
+        fake = (wl.WALL, 0.0, 0.0)
+        sides = (c.sides[0] if xa == 0 else fake, c.sides[1] if xb == n else fake,
+                 c.sides[2] if ya == 0 else fake, c.sides[3] if yb == n else fake)
+        win = orc.Domain(xb - xa, yb - ya, c.nu, c.gamma, sides)
+        win.set_pops(np.ascontiguousarray(fprev[:, ya:yb, xa:xb]))
+        win.step(1)
+        ix, iy = x0 - xa, y0 - ya
+        ref = win.pops()[:, iy:iy + 12, ix:ix + 12] - W
+        got = fnext[:, y0:y0 + 12, x0:x0 + 12] - W
+        # spacing of the FP16 grid of 2^14 g at the oracle's value, in units of g
+        spacing = np.spacing(np.abs(ref * 16384.0).astype(np.float16)).astype(np.float64) / 16384.0
+        excess = max(excess, float((np.abs(got - ref) - spacing).max()))
+        signed.append(((got - ref) / spacing).ravel())
+    signed = np.concatenate(signed)
+    assert excess < 5e-7, excess
+    assert abs(signed.mean()) < 0.02, signed.mean()
+
+
 def _window_check_periodic(fg_prev, fg_next, case, x0, y0, w, h):
     """As _window_check for a fully periodic domain: the window and its two-cell
     margin wrap around the domain's sides, so seams and corners are checked."""
