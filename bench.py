@@ -47,7 +47,8 @@ KERNEL_SOURCES = ["paper_1806_10251_gb300/csrc/stream_collide_x2.cuh",
                   "paper_1806_10251_gb300/csrc/collide_x2.cuh",
                   "paper_1806_10251_gb300/csrc/f32x2.cuh",
                   "paper_1806_10251_gb300/csrc/stream_collide.cuh",
-                  "paper_1806_10251_gb300/csrc/d2q9_collide.cuh"]
+                  "paper_1806_10251_gb300/csrc/d2q9_collide.cuh",
+                  "paper_1806_10251_gb300/csrc/open_bc.cuh"]
 
 
 def parse():
@@ -91,6 +92,10 @@ def parse():
     ap.add_argument("--cyl-d", type=int, default=16, help="cylinder: side of the square cylinder in cells")
     ap.add_argument("--serve-wall-s", type=float, default=600.0,
                     help="serve: the session ends this long after the first arrival (what is left is cancelled)")
+    ap.add_argument("--admission", type=int, choices=[0, 1], default=1,
+                    help="serve: 0 first come first served, 1 smallest domain first")
+    ap.add_argument("--max-running-cells", type=float, default=32e6,
+                    help="serve: admit while the running domains hold at most this many cells (0: no cap)")
     ap.add_argument("--side-min", type=int, default=128)
     ap.add_argument("--side-max", type=int, default=512)
     ap.add_argument("--scale", type=int, default=16,
@@ -414,6 +419,8 @@ def run_serve(args, rank):
     budget = 24 << 30
     b = lbm.Batch(budget, storage=lbm.STORAGE_F16)
     b.set_option("check_every", args.check_every)
+    b.set_option("admission", args.admission)
+    b.set_option("max_running_cells", args.max_running_cells)
     b.start()
     t0 = time.perf_counter()
     ids, kinds, pending, done = [], {}, set(), {}
@@ -487,6 +494,8 @@ def run_serve(args, rank):
             "config": {"rate_per_s": args.rate, "requests": args.requests, "side": [args.side_min, args.side_max],
                        "request_max_steps": args.request_max_steps, "session_wall_s": args.serve_wall_s,
                        "tol": args.tol, "check_every": args.check_every,
+                       "admission": ["first come first served", "smallest domain first"][args.admission],
+                       "max_running_cells": args.max_running_cells, "ticks": stats["ticks"],
                        "check_rule": "per request: check_interval (8 transits)", "budget_bytes": budget,
                        "stream": "poisson_requests(seed=0)"},
             "data": "synthetic"}

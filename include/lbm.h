@@ -269,6 +269,12 @@ typedef struct {
  * grid barrier between steps, launched directly -- FP32/FP16/BF16 storage,
  * full GI kernel, running domains of one force variant; otherwise per-step
  * launches),
+ * "admission" (0, default: first come first served; 1: the smallest queued
+ * domain, by cell count, first -- the oldest among equals), "max_running_cells"
+ * (0, default: no cap; else a request is admitted only while the running
+ * domains and it hold at most this many cells, or when nothing runs: the cap
+ * bounds the time of a step of the batch and so of a tick, which is the
+ * granularity of admission, retirement and cancellation),
  * "stochastic_rounding" (as lbm_set_option, default 1, for domains admitted
  * afterwards), "average_samples" (M, set before the first submit; default 16
  * for FP16/BF16 storage, 0 otherwise): the velocity of every domain is sampled

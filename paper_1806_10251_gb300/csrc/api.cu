@@ -27,6 +27,43 @@ lbm_status fail(lbm_status s, const std::string &msg)
 
 lbm_status lbm::set_error(lbm_status s, const std::string &msg) { return fail(s, msg); }
 
+// solid_rows: for each row r and 32-column block b, whether a solid cell lies in
+// rows r - 1 .. r + 1 and columns 32 b - 34 .. 32 b + 65 (blocks b - 1 .. b + 1
+// with the two columns each way that a strip's halo pulls reach); periodic
+// sides wrap, wall sides clip.  Row prefix sums answer each range.
+std::vector<uint8_t> lbm::make_solid_rows(const uint8_t *mask, int nx, int ny, bool perx, bool pery)
+{
+    const int nb = (nx + 31) / 32;
+    std::vector<int> pre((size_t)ny * (nx + 1), 0);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            pre[(size_t)y * (nx + 1) + x + 1] = pre[(size_t)y * (nx + 1) + x] + (mask[(size_t)y * nx + x] != 0);
+    auto count = [&](int y, int a, int b) -> int {  // solids of row y in columns a .. b (a <= b)
+        if (perx) {
+            if (b - a + 1 >= nx) return pre[(size_t)y * (nx + 1) + nx];
+            int aw = ((a % nx) + nx) % nx, bw = ((b % nx) + nx) % nx;
+            if (aw <= bw) return pre[(size_t)y * (nx + 1) + bw + 1] - pre[(size_t)y * (nx + 1) + aw];
+            return pre[(size_t)y * (nx + 1) + nx] - pre[(size_t)y * (nx + 1) + aw] + pre[(size_t)y * (nx + 1) + bw + 1];
+        }
+        a = a < 0 ? 0 : a;
+        b = b >= nx ? nx - 1 : b;
+        return a > b ? 0 : pre[(size_t)y * (nx + 1) + b + 1] - pre[(size_t)y * (nx + 1) + a];
+    };
+    std::vector<uint8_t> out((size_t)ny * nb, 0);
+    for (int y = 0; y < ny; ++y)
+        for (int b = 0; b < nb; ++b) {
+            int n = 0;
+            for (int dy = -1; dy <= 1 && !n; ++dy) {
+                int yy = y + dy;
+                if (pery) yy = (yy + ny) % ny;
+                if (yy < 0 || yy >= ny) continue;
+                n += count(yy, 32 * b - 34, 32 * b + 65);
+            }
+            out[(size_t)y * nb + b] = n ? 1 : 0;
+        }
+    return out;
+}
+
 namespace {
 
 lbm_status cuda_fail(cudaError_t e, const char *where)
@@ -79,6 +116,7 @@ struct lbm_ctx {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *d_solid = nullptr;
+    uint8_t *d_solid_rows = nullptr;  // rows whose strips meet a solid (see make_solid_rows)
     float *d_force = nullptr;
     double *d_snap_ux = nullptr, *d_snap_uy = nullptr, *d_partials = nullptr, *d_result = nullptr;
     unsigned long long *d_guard = nullptr;
@@ -149,6 +187,7 @@ StepParams make_params(const lbm_ctx *c)
     p.Fy = c->Fy;
     p.force = c->d_force;
     p.solid = c->d_solid;
+    p.solid_rows = c->d_solid_rows;
     p.guard_count = c->d_guard;
     p.error = c->d_err;
     p.work = c->d_work;
@@ -258,6 +297,7 @@ void free_ctx(lbm_ctx *c)
     dev_free(c->f[0]);
     dev_free(c->f[1]);
     dev_free(c->d_solid);
+    dev_free(c->d_solid_rows);
     dev_free(c->d_force);
     dev_free(c->d_snap_ux);
     dev_free(c->d_snap_uy);
@@ -422,6 +462,18 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const l
         if (e != cudaSuccess) {
             free_ctx(c);
             return cuda_fail(e, "cudaMemcpy(mask)");
+        }
+        const std::vector<uint8_t> rows = make_solid_rows(bnd->solid, nx, ny, sides[0].kind == LBM_SIDE_PERIODIC,
+                                                          sides[2].kind == LBM_SIDE_PERIODIC);
+        c->d_solid_rows = (uint8_t *)dev_alloc(rows.size());
+        if (!c->d_solid_rows) {
+            free_ctx(c);
+            return fail(LBM_ERR_OOM, "device allocation failed (mask rows)");
+        }
+        e = cudaMemcpy(c->d_solid_rows, rows.data(), rows.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_ctx(c);
+            return cuda_fail(e, "cudaMemcpy(mask rows)");
         }
     }
     e = build_tensor_maps(c);

@@ -65,6 +65,7 @@ struct Slot {
     void *f[2] = {nullptr, nullptr};
     double *snap = nullptr;  // 2 * nx * ny: ux then uy
     uint8_t *solid = nullptr;
+    uint8_t *solid_rows = nullptr;  // rows whose strips meet a solid (make_solid_rows)
     size_t bytes = 0;
     StepParams p{};
     bool forced = false;  // uniform body force: stepped by the forced kernel variant
@@ -122,6 +123,8 @@ struct lbm_batch {
     unsigned int *d_work = nullptr;
     unsigned int *d_ctl = nullptr;  // persistent kernel: item counters, barrier arrivals and generation
     int persistent_option = -1;     // -1: chosen by the autotuner, 0: per-step launches, 1: persistent
+    int admission = 0;              // 0: first come first served, 1: smallest domain first
+    double max_running_cells = 0;   // admit while the running domains hold fewer cells (0: no cap)
     int mode = 0;                   // current: 0 per-step launches, 1 persistent kernel
     int *d_err = nullptr;
     double *d_sums = nullptr, *d_partials = nullptr, *h_sums = nullptr;
@@ -181,6 +184,7 @@ void free_slot(Slot &s)
     if (s.f[1]) cudaFree(s.f[1]);
     if (s.snap) cudaFree(s.snap);
     if (s.solid) cudaFree(s.solid);
+    if (s.solid_rows) cudaFree(s.solid_rows);
     if (s.acc) cudaFree(s.acc);
     s = Slot();
 }
@@ -226,6 +230,15 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
             free_slot(s);
             return LBM_ERR_CUDA;
         }
+        const bool px = r.use_bnd && r.bnd.west.kind == LBM_SIDE_PERIODIC;
+        const bool py = r.use_bnd && r.bnd.south.kind == LBM_SIDE_PERIODIC;
+        const std::vector<uint8_t> rows = make_solid_rows(q.solid.data(), r.nx, r.ny, px, py);
+        if (cudaMalloc((void **)&s.solid_rows, rows.size()) != cudaSuccess ||
+            cudaMemcpy(s.solid_rows, rows.data(), rows.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            free_slot(s);
+            return LBM_ERR_OOM;
+        }
     }
     // parameters (the same derivation as lbm_create / make_params)
     lbm_side sides[4];
@@ -264,6 +277,7 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     p.Fx = r.fx;
     p.Fy = r.fy;
     p.solid = s.solid;
+    p.solid_rows = s.solid_rows;
     p.sround = b->sround;
     p.cf.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
     p.cd.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
@@ -314,17 +328,32 @@ void admit_pending(lbm_batch *b)
         {
             std::lock_guard<std::mutex> lk(b->mu);
             if (b->queue.empty()) return;
-            const Pending &head = b->queue.front();
+            // the next request: the oldest, or the oldest of the smallest domains
+            size_t pick = 0;
+            if (b->admission == 1)
+                for (size_t i = 1; i < b->queue.size(); ++i)
+                    if ((long long)b->queue[i].req.nx * b->queue[i].req.ny <
+                        (long long)b->queue[pick].req.nx * b->queue[pick].req.ny)
+                        pick = i;
+            const Pending &head = b->queue[pick];
+            if (b->max_running_cells > 0) {
+                double run = 0;
+                for (const Slot &s : b->slots)
+                    if (s.used && s.running) run += (double)s.nx * s.ny;
+                // the cap bounds the step time (so the tick, admission and
+                // cancellation latency); an empty batch admits any request
+                if (run > 0 && run + (double)head.req.nx * head.req.ny > b->max_running_cells) return;
+            }
             const size_t need = footprint(b, head.req.nx, head.req.ny, !head.solid.empty());
-            if (b->used + need > b->budget) return;  // FIFO: the head waits for memory
+            if (b->used + need > b->budget) return;  // the pick waits for memory
             for (int k = 0; k < b->max_slots; ++k)
                 if (!b->slots[k].used) {
                     si = k;
                     break;
                 }
             if (si < 0) return;
-            q = std::move(b->queue.front());
-            b->queue.pop_front();
+            q = std::move(b->queue[pick]);
+            b->queue.erase(b->queue.begin() + (long)pick);
             b->slots[si].used = true;  // reserve
             b->used += need;
         }
@@ -807,6 +836,18 @@ lbm_status lbm_batch_set_option(lbm_batch *b, const char *key, double v)
         b->persistent_option = (int)v;  // run_mu held: not during a tick
         b->mode = v == 1.0 ? 1 : 0;
         b->tuned = false;
+        return LBM_OK;
+    }
+    if (k == "admission") {
+        if (v != 0.0 && v != 1.0) return bfail(LBM_ERR_INVALID, "admission must be 0 or 1");
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->admission = (int)v;
+        return LBM_OK;
+    }
+    if (k == "max_running_cells") {
+        if (!(v >= 0) || !isfinite(v)) return bfail(LBM_ERR_INVALID, "max_running_cells must be >= 0");
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->max_running_cells = v;
         return LBM_OK;
     }
     if (k == "average_samples") {

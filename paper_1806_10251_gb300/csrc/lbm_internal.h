@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 
@@ -177,6 +178,11 @@ struct StepParams {
     double Fx, Fy;           // uniform force
     const float *force;      // optional per-cell force: [2][ny][pitch] (fx, fy)
     const uint8_t *solid;    // optional mask [ny][pitch], 1 = solid
+    // with a mask: [ny][ceil(nx / 32)], nonzero when a solid cell lies within
+    // rows y - 1 .. y + 1 and the columns of 32-column blocks b - 1 .. b + 1
+    // (plus two columns each way): the rows whose strips must take the
+    // general pull (see solid_near)
+    const uint8_t *solid_rows;
     unsigned long long *guard_count;  // device counter, may be null
     int *error;              // device flag: set when a bounded wait expires
     unsigned int *work;      // device work counters {next item, warps done}, zero between launches
@@ -283,6 +289,10 @@ cudaError_t launch_pops_from_f64(const StepParams &p, int storage, const double 
                                  cudaStream_t s);
 
 size_t storage_bytes(int storage);
+
+// Host: the solid_rows table of StepParams from a host mask [ny][nx] (sides
+// periodic in x / y wrap).
+std::vector<uint8_t> make_solid_rows(const uint8_t *mask, int nx, int ny, bool perx, bool pery);
 
 // Record a message for lbm_last_error() on this thread and return the status.
 lbm_status set_error(lbm_status s, const std::string &msg);

@@ -123,6 +123,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// Whether row r of the strip covering 32-column blocks b0 .. b1 can meet a
+// solid cell in its pulls, its halo columns or its density stencil (the
+// solid_rows table); rows beyond a wall side have no cells.
+__device__ __forceinline__ bool solid_near(const StepParams &p, int r, int b0, int b1)
+{
+    if (!p.solid_rows) return true;  // no table: every row takes the general pull
+    if (p.pery) r = wrap(r, p.ny);
+    if (r < 0 || r >= p.ny) return false;
+    const int nb = (p.nx + 31) >> 5;
+    const uint8_t *row = p.solid_rows + (size_t)r * nb;
+    bool any = false;
+    for (int b = b0; b <= b1 && b < nb; ++b) any = any || row[b] != 0;
+    return any;
+}
+
 template <typename R> __device__ __forceinline__ const Consts<R> &consts(const StepParams &p);
 template <> __device__ __forceinline__ const Consts<float> &consts<float>(const StepParams &p) { return p.cf; }
 template <> __device__ __forceinline__ const Consts<double> &consts<double>(const StepParams &p) { return p.cd; }
@@ -313,7 +328,7 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
         // source lies beyond the wall; domains with solids take the general path.
         auto produce = [&](auto fast_tag, int r, R(&g)[9], bool &valid, R &rho, R &rho_l, R &rho_r) {
             constexpr bool FAST = decltype(fast_tag)::value;
-            if (FAST || !has_solid) {
+            if (FAST || !has_solid || !solid_near(p, r, strip, strip)) {
                 const bool row_in = FAST || p.pery || (r >= 0 && r < p.ny);
                 if (!row_in) {
 #pragma unroll

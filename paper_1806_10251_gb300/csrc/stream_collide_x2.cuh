@@ -325,7 +325,7 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
     // valid: bit c set when cell xe + c is a lattice site of the domain.
     auto produce = [&](auto fast_tag, int r, F2(&g)[9], int &valid, F2 &rho, R &rho_l, R &rho_r) {
         constexpr bool FAST = decltype(fast_tag)::value;
-        if (FAST || !has_solid) {
+        if (FAST || !has_solid || !solid_near(p, r, 2 * strip, 2 * strip + 1)) {
             const bool row_in = FAST || p.pery || (r >= 0 && r < p.ny);
             if (!row_in) {
 #pragma unroll

@@ -457,3 +457,49 @@ def test_persistent_option_with_mixed_force_variants_runs_per_step():
         m = fluid(c)
         assert max(np.abs(ug - uo)[m].max(), np.abs(vg - vo)[m].max()) < 2e-6, c.name
     b.close()
+
+
+def test_smallest_first_admission_under_a_cell_cap():
+    """admission = 1 with max_running_cells = 2 * 64^2: of a queue holding a
+    128^2, two 64^2 and a 96^2 cavity (submitted in that order before the first
+    tick), the two 64^2 run first, side by side; the 96^2 (over the cap beside
+    them) waits for both to finish, the 128^2 for the 96^2; first come first
+    served with the same cap admits the 128^2 first, alone.  The results are
+    those of each domain alone."""
+    sides = (128, 64, 64, 96)
+    cases = [wl.cavity(n, 100.0, 0.1, 0.5) for n in sides]
+
+    def session(admission):
+        b = lbm.Batch(1 << 30, storage=lbm.STORAGE_F32)
+        b.set_option("check_every", 100)
+        b.set_option("rows_per_item", 8)
+        b.set_option("admission", admission)
+        b.set_option("max_running_cells", 2 * 64 * 64)
+        ids = [b.submit_case(c, tol=1e-300, max_steps=400) for c in cases]
+        b.run()
+        res = [b.poll(r)[1] for r in ids]
+        fields = [b.fields(r, c.nx, c.ny) for r, c in zip(ids, cases)]
+        b.close()
+        return res, fields
+
+    res, fields = session(1)
+    big, s1, s2, mid = res
+    assert all(r.state == lbm.REQ_NOT_CONVERGED and r.steps == 400 for r in res)
+    assert s1.t_admit <= s2.t_admit < min(s1.t_done, s2.t_done)    # side by side
+    assert mid.t_admit >= max(s1.t_done, s2.t_done)                 # waits for both
+    assert big.t_admit >= mid.t_done
+    fifo, _ = session(0)
+    assert fifo[0].t_admit <= min(r.t_admit for r in fifo[1:])
+    assert min(r.t_admit for r in fifo[1:]) >= fifo[0].t_done
+    for c, f in zip(cases, fields):
+        alone = lbm.Batch(1 << 30, storage=lbm.STORAGE_F32)
+        alone.set_option("check_every", 100)
+        alone.set_option("rows_per_item", 8)
+        rid = alone.submit_case(c, tol=1e-300, max_steps=400)
+        alone.run()
+        g = alone.fields(rid, c.nx, c.ny)
+        alone.close()
+        for a, b_ in zip(f, g):
+            assert np.array_equal(a, b_, equal_nan=True), c.name
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch(1 << 26, storage=lbm.STORAGE_F32).set_option("admission", 2)

@@ -142,6 +142,29 @@ def test_obstacle_channel_with_uniform_force():
     assert np.all(np.isnan(ug[c.solid == 1]))
 
 
+@pytest.mark.parametrize("storage,tol", [(lbm.STORAGE_F32, 2e-6), (lbm.STORAGE_F64, 1e-12)])
+@pytest.mark.parametrize("periodic_y", [False, True])
+def test_scattered_solids_on_strip_seams(storage, tol, periodic_y):
+    """Single solid cells and short bars on the 32- and 64-column seams, beside
+    the walls and across the periodic wrap, in a ragged domain stepped from a
+    random state: rows whose strips meet no solid take the wall/periodic pull
+    and the others the per-cell pull, so a strip wrongly judged solid-free
+    (a seam column, a halo column two cells away, a row one cell away, the
+    wrap) would stream from a solid cell and fail the population bound."""
+    nx, ny = 301, 45
+    rnd = wl.random_periodic(nx, ny, 0.45, 0.03, seed=21)
+    solid = np.zeros((ny, nx), np.uint8)
+    for x, y in ((31, 10), (32, 20), (63, 5), (64, 30), (66, 12), (95, 0), (127, ny - 1), (129, 22),
+                 (190, 17), (255, 33), (258, 8), (nx - 1, 25), (0, 38)):
+        solid[y, x] = 1
+    solid[40, 160:164] = 1  # a bar inside one strip, rows 39 .. 41 flagged
+    solid[2:6, 222] = 1     # a column bar beside a strip's right halo
+    sides = wl.periodic_sides() if periodic_y else \
+        ((wl.PERIODIC, 0.0, 0.0), (wl.PERIODIC, 0.0, 0.0), (wl.WALL, 0.0, 0.0), (wl.WALL, 0.0, 0.0))
+    c = dataclasses.replace(rnd, name=f"seams{nx}x{ny}_py{int(periodic_y)}", sides=sides, solid=solid)
+    compare(c, 80, storage=storage, pop_tol=tol)
+
+
 def test_variable_force_field():
     c = wl.four_rolls_mill(64, 0.045, 20.0, 0.3)
     compare(c, 150)
