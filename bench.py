@@ -96,6 +96,7 @@ def parse():
                     help="serve: 0 first come first served, 1 smallest domain first")
     ap.add_argument("--max-running-cells", type=float, default=32e6,
                     help="serve: admit while the running domains hold at most this many cells (0: no cap)")
+    ap.add_argument("--lid-mach", type=float, default=0.05, help="gamma: lid speed over c_s")
     ap.add_argument("--side-min", type=int, default=128)
     ap.add_argument("--side-max", type=int, default=512)
     ap.add_argument("--scale", type=int, default=16,
@@ -607,7 +608,7 @@ def run_precision(args, rank):
 def run_gamma(args, rank):
     """Convergence acceleration by preconditioning (the paper's steady-state
     claim): the lid-driven cavity of side --n at --Re with the lid at Mach
-    0.05 (U = 0.05 c_s), for gamma = 1, 0.5, 0.25, 0.1, 0.05, all in one FP32
+    --lid-mach (U = Ma c_s), for gamma = 1, 0.5, 0.25, 0.1, 0.05, all in one FP32
     batch started from rest; a domain stops at the first check (--check-every
     steps apart) with r < --tol.  Reports the steps to steady state per gamma,
     their ratio to gamma = 1, and the relative L2 distance of each steady field
@@ -621,7 +622,7 @@ def run_gamma(args, rank):
     if rank != 0:
         return 0
     torch.cuda.set_device(0)
-    U = 0.05 / np.sqrt(3.0)
+    U = args.lid_mach / np.sqrt(3.0)
     gammas = [1.0, 0.5, 0.25, 0.1, 0.05]
     cases = [wl.cavity(args.n, args.Re, U, g) for g in gammas]
     b = lbm.Batch(16 << 30, storage=lbm.STORAGE_F32)
@@ -661,7 +662,7 @@ def run_gamma(args, rank):
                                               for r in runs),
             "unit": "x fewer steps than gamma = 1 (best converged gamma; a lower bound if gamma = 1 did not converge)",
             "higher_is_better": True, "runs": runs, "wall_s": wall,
-            "config": {"n": args.n, "Re": args.Re, "U": U, "lid_mach": 0.05, "tol": args.tol,
+            "config": {"n": args.n, "Re": args.Re, "U": U, "lid_mach": args.lid_mach, "tol": args.tol,
                        "check_every": args.check_every, "max_steps": args.max_steps, "storage": "f32", "gi_mode": "full"},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)

@@ -20,43 +20,31 @@ namespace lbm {
 // Slot of direction a (one of 3, 6, 7: e_x = -1) in the outlet ghost column.
 __device__ __forceinline__ int ghost_slot(int a) { return a == 3 ? 0 : (a == 6 ? 1 : 2); }
 
-// Population a entering through an open side (side 0: parabolic inlet, side
-// 1: convective outlet) for a cell whose source row is sy: on the outlet, the
-// ghost column's incoming population; on the inlet, half-way bounce-back of
-// own_opp with the moving-wall term 6 w_a rho0 (e_a . u_w), u_w taken at the
-// height where the link crosses the inlet plane.  Out of line: only the edge
-// columns of open-sided domains call it, and the wall rows' inline code stays
-// small.
-template <typename R>
-__device__ __noinline__ R open_side_value(const StepParams &p, const Consts<R> &c, int a, int sy, int side, R own_opp)
-{
-    if (side == 1) {
-        const int gy = !p.pery ? sy : (sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy));
-        const long long gi = (long long)(2 + ghost_slot(a)) * p.ny + gy;
-        return LBM_IN_BOUNDS(gi, 5LL * p.ny, p.error) ? static_cast<const R *>(p.ghost_in)[gi] : own_opp;
-    }
-    const int ex = cx(a), ey = cy(a);
-    const R wa = a == 0 ? R(4.0 / 9.0) : (a <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
-    // 4 U_max t (H - t) / H^2 with t = y_cross + 1/2, y_cross = sy + e_y / 2
-    const R t = R(sy) + R(0.5) * R(ey) + R(0.5);
-    const R uw = c.wall6[0][0] * (c.inlet_k * t * (c.H - t));
-    return own_opp + wa * (R(ex) * uw + R(ey) * c.wall6[0][1]);
-}
-
 // Population a of a cell whose source (sx, sy) lies beyond the outx / outy
-// side(s) of the domain: on an open side, open_side_value; otherwise half-way
-// bounce-back of the cell's opposite population own_opp with the moving-wall
-// term 6 w_a rho0 (e_a . u_w).  A source beyond two sides (a corner) sees a
-// stationary wall.
+// side(s) of the domain: on a convective-outlet east side, the ghost column's
+// incoming population; otherwise half-way bounce-back of the cell's opposite
+// population own_opp with the moving-wall term 6 w_a rho0 (e_a . u_w), where a
+// parabolic inlet (west side) takes u_w at the height where the link crosses
+// the inlet plane.  A source beyond two sides (a corner) sees a stationary wall.
 template <typename R>
 __device__ __forceinline__ R boundary_value(const StepParams &p, const Consts<R> &c, int a, int ex, int ey, int sx,
                                             int sy, bool outx, bool outy, R own_opp)
 {
     if (outx == outy) return own_opp;
     const int side = outx ? (sx < 0 ? 0 : 1) : (sy < 0 ? 2 : 3);
-    if ((side == 1 && p.outlet) || (side == 0 && p.inlet)) return open_side_value<R>(p, c, a, sy, side, own_opp);
+    if (side == 1 && p.outlet) {
+        const int gy = !p.pery ? sy : (sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy));
+        const long long gi = (long long)(2 + ghost_slot(a)) * p.ny + gy;
+        return LBM_IN_BOUNDS(gi, 5LL * p.ny, p.error) ? static_cast<const R *>(p.ghost_in)[gi] : own_opp;
+    }
     const R wa = a == 0 ? R(4.0 / 9.0) : (a <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
-    return own_opp + wa * (R(ex) * c.wall6[side][0] + R(ey) * c.wall6[side][1]);
+    R uw = c.wall6[side][0];
+    if (side == 0 && p.inlet) {
+        // 4 U_max t (H - t) / H^2 with t = y_cross + 1/2, y_cross = sy + e_y / 2
+        const R t = R(sy) + R(0.5) * R(ey) + R(0.5);
+        uw = uw * (c.inlet_k * t * (c.H - t));
+    }
+    return own_opp + wa * (R(ex) * uw + R(ey) * c.wall6[side][1]);
 }
 
 // Deviations f_eq - w of directions 3, 6, 7 of the preconditioned equilibrium
@@ -113,10 +101,9 @@ __device__ __forceinline__ void outlet_row(const Consts<R> &c, int ny, int y, co
 
 // Convective outlet, row y, after the collision of the last column: advance
 // the ghost velocity, u_g <- u_g + U (u - u_g) (d_t u + U d_x u = 0, explicit
-// and upwind in lattice units), then the incoming populations.  Out of line
-// (one lane per row of the last strip calls it).
+// and upwind in lattice units), then the incoming populations.
 template <typename R>
-__device__ __noinline__ void outlet_update(const StepParams &p, const Consts<R> &c, int y, const R (&g)[9], R Fx,
+__device__ __forceinline__ void outlet_update(const StepParams &p, const Consts<R> &c, int y, const R (&g)[9], R Fx,
                                               R Fy)
 {
     if (!LBM_IN_BOUNDS(y, p.ny, p.error)) return;
