@@ -222,12 +222,15 @@ lbm_status lbm_kernel_launches(lbm_ctx *ctx, long *launches);
  * A batch keeps many independent domains resident and advances all running
  * ones together: one launch of the batched step kernel is one step (Eq. 2) of
  * every running domain, the work list spanning all their (strip, row segment)
- * items.  K steps (the check interval) are replayed from one captured CUDA
- * graph; after each replay every running domain's convergence residual (as in
- * lbm_run_to_steady) is checked in FP64, and converged, diverged or exhausted
- * domains retire while the others go on (per-domain masking).  Requests wait in
- * a FIFO queue and are admitted when their device footprint fits the batch's
- * memory budget; finished requests keep their populations until released.
+ * items.  A tick of K steps is replayed from one captured CUDA graph (or run
+ * by the persistent kernel, option "persistent"); after each tick the
+ * convergence residual (as in lbm_run_to_steady) of every running domain whose
+ * own check interval has passed is computed in FP64, and converged, diverged or
+ * exhausted domains retire while the others go on (per-domain masking).
+ * Requests wait in a queue and are admitted, in arrival order or smallest
+ * first (option "admission"), when their device footprint fits the batch's
+ * memory budget (and the option "max_running_cells"); finished requests keep
+ * their populations until released.
  * Storage and collision kernel are per batch; the device memory of a batch is
  * allocated with cudaMalloc.  A domain's results do not depend on the other
  * domains in the batch.  submit/poll/fields/release may be called from any
@@ -259,7 +262,7 @@ typedef struct {
 
 /* storage: LBM_STORAGE_*; gi_mode: LBM_GI_*; hbm_budget_bytes bounds the sum of
  * the admitted requests' footprints (2 population buffers + residual snapshot
- * + mask, + the window sums below).  Options: "check_every" (K, even, default
+ * + mask and its row table, + the window sums below).  Options: "check_every" (K, even, default
  * 1000: steps between convergence checks, one CUDA graph of K launches),
  * "rows_per_item" (rows of a warp's work item; 0 = chosen by timing a few
  * steps whenever the running work has changed by more than 2x), "persistent"

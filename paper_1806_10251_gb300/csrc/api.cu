@@ -27,7 +27,7 @@ lbm_status fail(lbm_status s, const std::string &msg)
 
 lbm_status lbm::set_error(lbm_status s, const std::string &msg) { return fail(s, msg); }
 
-// solid_rows: for each row r and 32-column block b, whether a solid cell lies in
+// The row table of a mask: for each row r and 32-column block b, whether a solid cell lies in
 // rows r - 1 .. r + 1 and columns 32 b - 34 .. 32 b + 65 (blocks b - 1 .. b + 1
 // with the two columns each way that a strip's halo pulls reach); periodic
 // sides wrap, wall sides clip.  Row prefix sums answer each range.
@@ -62,6 +62,16 @@ std::vector<uint8_t> lbm::make_solid_rows(const uint8_t *mask, int nx, int ny, b
             out[(size_t)y * nb + b] = n ? 1 : 0;
         }
     return out;
+}
+
+std::vector<uint8_t> lbm::mask_with_row_table(const uint8_t *mask, int nx, int ny, int pitch, bool perx, bool pery)
+{
+    const std::vector<uint8_t> rows = make_solid_rows(mask, nx, ny, perx, pery);
+    std::vector<uint8_t> h((size_t)pitch * ny + rows.size(), 0);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) h[(size_t)y * pitch + x] = mask[(size_t)y * nx + x] ? 1 : 0;
+    memcpy(h.data() + (size_t)pitch * ny, rows.data(), rows.size());
+    return h;
 }
 
 namespace {
@@ -116,7 +126,6 @@ struct lbm_ctx {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *d_solid = nullptr;
-    uint8_t *d_solid_rows = nullptr;  // rows whose strips meet a solid (see make_solid_rows)
     float *d_force = nullptr;
     double *d_snap_ux = nullptr, *d_snap_uy = nullptr, *d_partials = nullptr, *d_result = nullptr;
     unsigned long long *d_guard = nullptr;
@@ -187,7 +196,6 @@ StepParams make_params(const lbm_ctx *c)
     p.Fy = c->Fy;
     p.force = c->d_force;
     p.solid = c->d_solid;
-    p.solid_rows = c->d_solid_rows;
     p.guard_count = c->d_guard;
     p.error = c->d_err;
     p.work = c->d_work;
@@ -297,7 +305,6 @@ void free_ctx(lbm_ctx *c)
     dev_free(c->f[0]);
     dev_free(c->f[1]);
     dev_free(c->d_solid);
-    dev_free(c->d_solid_rows);
     dev_free(c->d_force);
     dev_free(c->d_snap_ux);
     dev_free(c->d_snap_uy);
@@ -450,30 +457,19 @@ lbm_status lbm_create(int nx, int ny, double nu, double gamma, double U, const l
         return fail(LBM_ERR_OOM, "pinned host allocation failed");
     }
     if (bnd && bnd->solid) {
-        c->d_solid = (uint8_t *)dev_alloc((size_t)c->pitch * ny);
+        // the mask [ny][pitch] and, after it, its row table (make_solid_rows)
+        const std::vector<uint8_t> h = mask_with_row_table(bnd->solid, nx, ny, c->pitch,
+                                                           sides[0].kind == LBM_SIDE_PERIODIC,
+                                                           sides[2].kind == LBM_SIDE_PERIODIC);
+        c->d_solid = (uint8_t *)dev_alloc(h.size());
         if (!c->d_solid) {
             free_ctx(c);
             return fail(LBM_ERR_OOM, "device allocation failed (mask)");
         }
-        std::vector<uint8_t> h((size_t)c->pitch * ny, 0);
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) h[(size_t)y * c->pitch + x] = bnd->solid[(size_t)y * nx + x] ? 1 : 0;
         e = cudaMemcpy(c->d_solid, h.data(), h.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             free_ctx(c);
             return cuda_fail(e, "cudaMemcpy(mask)");
-        }
-        const std::vector<uint8_t> rows = make_solid_rows(bnd->solid, nx, ny, sides[0].kind == LBM_SIDE_PERIODIC,
-                                                          sides[2].kind == LBM_SIDE_PERIODIC);
-        c->d_solid_rows = (uint8_t *)dev_alloc(rows.size());
-        if (!c->d_solid_rows) {
-            free_ctx(c);
-            return fail(LBM_ERR_OOM, "device allocation failed (mask rows)");
-        }
-        e = cudaMemcpy(c->d_solid_rows, rows.data(), rows.size(), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            free_ctx(c);
-            return cuda_fail(e, "cudaMemcpy(mask rows)");
         }
     }
     e = build_tensor_maps(c);

@@ -65,7 +65,6 @@ struct Slot {
     void *f[2] = {nullptr, nullptr};
     double *snap = nullptr;  // 2 * nx * ny: ux then uy
     uint8_t *solid = nullptr;
-    uint8_t *solid_rows = nullptr;  // rows whose strips meet a solid (make_solid_rows)
     size_t bytes = 0;
     StepParams p{};
     bool forced = false;  // uniform body force: stepped by the forced kernel variant
@@ -175,7 +174,7 @@ size_t footprint(const lbm_batch *b, int nx, int ny, bool solid)
     const size_t plane = pitch * ny;
     const size_t snaps = samples_per_tick(b) > 0 ? 4 : 2;  // snapshot (+ window sums) in FP64
     return 2 * 9 * plane * storage_bytes(b->storage) + snaps * (size_t)nx * ny * sizeof(double) +
-           (solid ? plane : 0);
+           (solid ? plane + (size_t)ny * ((nx + 31) / 32) : 0);  // mask + its row table
 }
 
 void free_slot(Slot &s)
@@ -184,7 +183,6 @@ void free_slot(Slot &s)
     if (s.f[1]) cudaFree(s.f[1]);
     if (s.snap) cudaFree(s.snap);
     if (s.solid) cudaFree(s.solid);
-    if (s.solid_rows) cudaFree(s.solid_rows);
     if (s.acc) cudaFree(s.acc);
     s = Slot();
 }
@@ -214,31 +212,22 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     const size_t pb = 9 * (size_t)s.plane * storage_bytes(b->storage);
     const size_t N = (size_t)r.nx * r.ny;
     const bool avg = samples_per_tick(b) > 0;
+    // the mask [ny][pitch] and, after it, its row table (make_solid_rows)
+    std::vector<uint8_t> mask;
+    if (!q.solid.empty())
+        mask = mask_with_row_table(q.solid.data(), r.nx, r.ny, s.pitch, r.use_bnd && r.bnd.west.kind == LBM_SIDE_PERIODIC,
+                                   r.use_bnd && r.bnd.south.kind == LBM_SIDE_PERIODIC);
     if (cudaMalloc(&s.f[0], pb) != cudaSuccess || cudaMalloc(&s.f[1], pb) != cudaSuccess ||
         cudaMalloc((void **)&s.snap, 2 * N * sizeof(double)) != cudaSuccess ||
         (avg && cudaMalloc((void **)&s.acc, 2 * N * sizeof(double)) != cudaSuccess) ||
-        (!q.solid.empty() && cudaMalloc((void **)&s.solid, (size_t)s.plane) != cudaSuccess)) {
+        (!mask.empty() && cudaMalloc((void **)&s.solid, mask.size()) != cudaSuccess)) {
         cudaGetLastError();
         free_slot(s);
         return LBM_ERR_OOM;
     }
-    if (s.solid) {
-        std::vector<uint8_t> h((size_t)s.plane, 0);
-        for (int y = 0; y < r.ny; ++y)
-            for (int x = 0; x < r.nx; ++x) h[(size_t)y * s.pitch + x] = q.solid[(size_t)y * r.nx + x] ? 1 : 0;
-        if (cudaMemcpy(s.solid, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-            free_slot(s);
-            return LBM_ERR_CUDA;
-        }
-        const bool px = r.use_bnd && r.bnd.west.kind == LBM_SIDE_PERIODIC;
-        const bool py = r.use_bnd && r.bnd.south.kind == LBM_SIDE_PERIODIC;
-        const std::vector<uint8_t> rows = make_solid_rows(q.solid.data(), r.nx, r.ny, px, py);
-        if (cudaMalloc((void **)&s.solid_rows, rows.size()) != cudaSuccess ||
-            cudaMemcpy(s.solid_rows, rows.data(), rows.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaGetLastError();
-            free_slot(s);
-            return LBM_ERR_OOM;
-        }
+    if (s.solid && cudaMemcpy(s.solid, mask.data(), mask.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        free_slot(s);
+        return LBM_ERR_CUDA;
     }
     // parameters (the same derivation as lbm_create / make_params)
     lbm_side sides[4];
@@ -277,7 +266,6 @@ lbm_status admit(lbm_batch *b, int si, const Pending &q)
     p.Fx = r.fx;
     p.Fy = r.fy;
     p.solid = s.solid;
-    p.solid_rows = s.solid_rows;
     p.sround = b->sround;
     p.cf.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);
     p.cd.set(r.gamma, w, b->gi_mode, r.fx, r.fy, p.side_u);

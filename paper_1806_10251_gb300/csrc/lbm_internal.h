@@ -177,12 +177,12 @@ struct StepParams {
     void *ghost_out;
     double Fx, Fy;           // uniform force
     const float *force;      // optional per-cell force: [2][ny][pitch] (fx, fy)
-    const uint8_t *solid;    // optional mask [ny][pitch], 1 = solid
-    // with a mask: [ny][ceil(nx / 32)], nonzero when a solid cell lies within
+    // optional mask [ny][pitch], 1 = solid, followed in the same allocation by
+    // its row table [ny][ceil(nx / 32)]: nonzero when a solid cell lies within
     // rows y - 1 .. y + 1 and the columns of 32-column blocks b - 1 .. b + 1
-    // (plus two columns each way): the rows whose strips must take the
-    // general pull (see solid_near)
-    const uint8_t *solid_rows;
+    // (plus two columns each way); a work item whose rows meet none takes the
+    // paths of a domain without a mask (item_meets_solid)
+    const uint8_t *solid;
     unsigned long long *guard_count;  // device counter, may be null
     int *error;              // device flag: set when a bounded wait expires
     unsigned int *work;      // device work counters {next item, warps done}, zero between launches
@@ -290,9 +290,12 @@ cudaError_t launch_pops_from_f64(const StepParams &p, int storage, const double 
 
 size_t storage_bytes(int storage);
 
-// Host: the solid_rows table of StepParams from a host mask [ny][nx] (sides
-// periodic in x / y wrap).
+// Host: the row table of a mask (see StepParams::solid) from a host mask
+// [ny][nx] (sides periodic in x / y wrap).
 std::vector<uint8_t> make_solid_rows(const uint8_t *mask, int nx, int ny, bool perx, bool pery);
+// Host: the device layout of StepParams::solid from a host mask [ny][nx]: the
+// mask as 0/1 bytes [ny][pitch], then its row table.
+std::vector<uint8_t> mask_with_row_table(const uint8_t *mask, int nx, int ny, int pitch, bool perx, bool pery);
 
 // Record a message for lbm_last_error() on this thread and return the status.
 lbm_status set_error(lbm_status s, const std::string &msg);

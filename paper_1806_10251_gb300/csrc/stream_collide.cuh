@@ -123,18 +123,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Whether row r of the strip covering 32-column blocks b0 .. b1 can meet a
-// solid cell in its pulls, its halo columns or its density stencil (the
-// solid_rows table); rows beyond a wall side have no cells.
-__device__ __forceinline__ bool solid_near(const StepParams &p, int r, int b0, int b1)
+// Whether the work item of columns x0 .. x0 + w - 1 (w = 32 or 64) and rows
+// y0 .. y1 - 1 can meet a solid cell: in the pulls, halo columns and density
+// stencils of the rows it produces (y0 - 1 .. y1), which the mask's row table
+// (after the mask, StepParams::solid) answers per row and 32-column block.
+// Warp-uniform (lane k looks at rows y0 - 1 + k, y0 + 31 + k, ...).  An item
+// that meets none takes the paths of a domain without a mask.
+__device__ __forceinline__ bool item_meets_solid(const StepParams &p, int x0, int y0, int y1, int lane, int w = 64)
 {
-    if (!p.solid_rows) return true;  // no table: every row takes the general pull
-    if (p.pery) r = wrap(r, p.ny);
-    if (r < 0 || r >= p.ny) return false;
+    if (!p.solid) return false;
+    const uint8_t *table = p.solid + (size_t)p.ny * p.pitch;
     const int nb = (p.nx + 31) >> 5;
-    const uint8_t *row = p.solid_rows + (size_t)r * nb;
+    const int b0 = x0 >> 5, b1 = min(b0 + (w >> 5) - 1, nb - 1);
     bool any = false;
-    for (int b = b0; b <= b1 && b < nb; ++b) any = any || row[b] != 0;
+    for (int r0 = y0 - 1; r0 <= y1; r0 += 32) {
+        int r = r0 + lane;
+        bool f = false;
+        if (r <= y1) {
+            if (p.pery) r = wrap(r, p.ny);
+            if (r >= 0 && r < p.ny) {
+                const uint8_t *row = table + (size_t)r * nb;
+                for (int b = b0; b <= b1; ++b) f = f || row[b] != 0;
+            }
+        }
+        any = any || __any_sync(0xffffffffu, f);
+    }
     return any;
 }
 
@@ -210,7 +223,6 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
     int &issued = w.issued;
     const int h_side = w.h_side, h_a = w.h_a, h_ex = w.h_ex, h_ey = w.h_ey;
     const Consts<R> &c = consts<R>(p);
-    const bool has_solid = p.solid != nullptr;
     const bool sround = StorageTraits<ST>::kReduced && p.sround;
     const uint32_t seed = sround ? mix32(step) : 0u;
     bool abort = false;
@@ -218,6 +230,8 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
         const int x0 = strip * WS;
         const int y0 = seg * p.Ly;
         const int y1 = min(y0 + p.Ly, p.ny);
+        // an item that meets no solid takes the paths of a domain without a mask
+        const bool has_solid = item_meets_solid(p, x0, y0, y1, lane, WS);
         const int s_first = y0 - 2;
         const int nsrc = (y1 + 1) - s_first + 1;  // source rows y0-2 .. y1+1
         const int x = x0 + lane;                  // this lane's cell
@@ -328,7 +342,7 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
         // source lies beyond the wall; domains with solids take the general path.
         auto produce = [&](auto fast_tag, int r, R(&g)[9], bool &valid, R &rho, R &rho_l, R &rho_r) {
             constexpr bool FAST = decltype(fast_tag)::value;
-            if (FAST || !has_solid || !solid_near(p, r, strip, strip)) {
+            if (FAST || !has_solid) {
                 const bool row_in = FAST || p.pery || (r >= 0 && r < p.ny);
                 if (!row_in) {
 #pragma unroll

@@ -207,13 +207,14 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
     int &issued = w.issued;
     const int h_side = w.h_side, h_a = w.h_a, h_ex = w.h_ex, h_ey = w.h_ey;
     const Consts<float> &c = p.cf;
-    const bool has_solid = p.solid != nullptr;
     const bool sround = StorageTraits<ST>::kReduced && p.sround;
     const uint32_t seed = sround ? mix32(step) : 0u;
 
     const int x0 = strip * SW;
     const int y0 = seg * p.Ly;
     const int y1 = min(y0 + p.Ly, p.ny);
+    // an item that meets no solid takes the paths of a domain without a mask
+    const bool has_solid = item_meets_solid(p, x0, y0, y1, lane);
     const int s_first = y0 - 2;
     const int nsrc = (y1 + 1) - s_first + 1;  // source rows y0-2 .. y1+1
     const int xe = x0 + 2 * lane;             // this lane's even cell; the odd one is xe + 1
@@ -325,7 +326,7 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
     // valid: bit c set when cell xe + c is a lattice site of the domain.
     auto produce = [&](auto fast_tag, int r, F2(&g)[9], int &valid, F2 &rho, R &rho_l, R &rho_r) {
         constexpr bool FAST = decltype(fast_tag)::value;
-        if (FAST || !has_solid || !solid_near(p, r, 2 * strip, 2 * strip + 1)) {
+        if (FAST || !has_solid) {
             const bool row_in = FAST || p.pery || (r >= 0 && r < p.ny);
             if (!row_in) {
 #pragma unroll

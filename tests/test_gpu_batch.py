@@ -503,3 +503,27 @@ def test_smallest_first_admission_under_a_cell_cap():
             assert np.array_equal(a, b_, equal_nan=True), c.name
     with pytest.raises(lbm.LbmError):
         lbm.Batch(1 << 26, storage=lbm.STORAGE_F32).set_option("admission", 2)
+
+
+def test_large_batch_domains_agree_with_the_single_domain_kernel():
+    """Config-4-sized domains in one batch: a 1024^2 cavity, a ragged 1000 x 600
+    cavity and a 1024 x 256 obstacle channel (solid row table), 200 FP32 steps,
+    against the single-domain kernel (whose 4096^2 launches match the oracle on
+    sampled windows, test_gpu_parity): the same fields to FP32 rounding (a
+    separately compiled kernel may contract differently)."""
+    cases = [wl.cavity(1024, 1000.0, 0.1, 0.3),
+             wl.cavity(1000, 400.0, 0.1, 0.7, ny=600),
+             wl.channel_obstacle(nx=1024, ny=256, D=16, Re=40.0, U0=0.05, gamma=0.5, xc=128)]
+    b = lbm.Batch(8 << 30, storage=lbm.STORAGE_F32)
+    b.set_option("check_every", 100)
+    _, fields = run_fixed(b, cases, 200)
+    b.close()
+    for c, f in zip(cases, fields):
+        g = lbm.solver_from_case(c)
+        g.step(200)
+        single = g.fields()
+        g.close()
+        m = fluid(c)
+        for k in range(3):
+            d = np.abs(f[k] - single[k])[m].max()
+            assert d < 2e-6, (c.name, k, d)
