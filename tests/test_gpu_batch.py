@@ -516,6 +516,7 @@ def test_large_batch_domains_agree_with_the_single_domain_kernel():
              wl.channel_obstacle(nx=1024, ny=256, D=16, Re=40.0, U0=0.05, gamma=0.5, xc=128)]
     b = lbm.Batch(8 << 30, storage=lbm.STORAGE_F32)
     b.set_option("check_every", 100)
+    b.set_option("rows_per_item", 16)  # no autotuning steps: exactly 200 steps
     _, fields = run_fixed(b, cases, 200)
     b.close()
     for c, f in zip(cases, fields):

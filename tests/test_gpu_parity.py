@@ -147,10 +147,11 @@ def test_obstacle_channel_with_uniform_force():
 def test_scattered_solids_on_strip_seams(storage, tol, periodic_y):
     """Single solid cells and short bars on the 32- and 64-column seams, beside
     the walls and across the periodic wrap, in a ragged domain stepped from a
-    random state: rows whose strips meet no solid take the wall/periodic pull
-    and the others the per-cell pull, so a strip wrongly judged solid-free
-    (a seam column, a halo column two cells away, a row one cell away, the
-    wrap) would stream from a solid cell and fail the population bound."""
+    random state: work items that meet no solid (by the mask's row table) take
+    the paths of an unmasked domain and the others the per-cell pull, so an
+    item wrongly judged solid-free (a seam column, a halo column two cells
+    away, a row one cell away, the wrap) would stream from a solid cell and
+    fail the population bound."""
     nx, ny = 301, 45
     rnd = wl.random_periodic(nx, ny, 0.45, 0.03, seed=21)
     solid = np.zeros((ny, nx), np.uint8)
