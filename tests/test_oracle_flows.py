@@ -223,6 +223,35 @@ def _four_rolls_oracle(c, gi_mode, chunk=500, tol=1e-11, max_steps=40000):
     return u, v
 
 
+def test_small_gamma_cavity_stability_follows_the_lid_effective_mach():
+    """The cavity of the convergence-acceleration study (Sec. 6: Re = 3200,
+    gamma = 0.05) on 200^2: with the lid at Mach 0.05 (U = 0.05 c_s, the lid's
+    effective Mach number U / (gamma c_s) = 1) the scheme blows up within a few
+    hundred steps for every bulk rate omega3 and every common omega6 = omega7 =
+    omega8 (the rates the paper does not give, reading A1), with and without
+    the corrections; with the lid at Mach 0.025 (effective Mach 0.5) the same
+    cavity stays bounded.  The instability is the lid's, not the rates'."""
+    cs = 1.0 / np.sqrt(3.0)
+
+    def blows_up(mach, gi_mode, w3=1.0, w678=1.0, steps=2000):
+        c = wl.cavity(200, 3200.0, mach * cs, 0.05)
+        d = orc.Domain(c.nx, c.ny, c.nu, c.gamma, c.sides, gi_mode=gi_mode, omega3=w3, omega6=w678,
+                       omega7=w678, omega8=w678)
+        d.init_equilibrium()
+        for _ in range(steps // 50):
+            d.step(50)
+            _, u, _ = d.fields()
+            if not np.isfinite(u).all() or np.abs(u).max() > 3 * c.U:
+                return True
+        return False
+
+    for gi in (orc.GI_UNCORRECTED, orc.GI_FULL):
+        assert not blows_up(0.025, gi)
+        assert blows_up(0.05, gi, steps=500)
+    for w3, w678 in ((1.5, 1.0), (1.9, 1.0), (0.8, 1.0), (1.0, 1.5), (1.0, 1.9), (1.0, 0.8)):
+        assert blows_up(0.05, orc.GI_FULL, w3, w678, steps=500), (w3, w678)
+
+
 def test_four_rolls_mill_incompressible_field_is_the_low_mach_limit():
     """The printed four-rolls field u0 (sin x sin y, cos x cos y) solves the
     incompressible equations (Sec. 6.5).  The scheme solves the preconditioned
