@@ -122,7 +122,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(storage: str, n: int):
+def profiled_traffic(storage: str, n: int, rows_per_item=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", f"stream_collide_{storage}_cavity{n}.txt")
@@ -135,6 +135,8 @@ def profiled_traffic(storage: str, n: int):
             vals[k.strip()] = v.strip()
     if vals.get("kernel_sources_sha256") != kernel_hash():
         return None
+    if rows_per_item is not None and vals.get("rows_per_item") not in (None, str(rows_per_item)):
+        return None  # another work decomposition than the one the counters were taken on
     try:
         return int(float(vals["dram_bytes_per_launch"]))
     except (KeyError, ValueError):
@@ -800,7 +802,7 @@ def main():
                        "l2": "no flush: populations (per replica) exceed the 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": profiled_traffic(args.storage, args.n),
+                         "traffic": profiled_traffic(args.storage, args.n, int(g.get_option("cells_per_item"))),
                          "bytes_per_cell": bpc,
                          "kernel": "stream_collide_kernel" if args.storage == "f64" else "stream_collide_x2_kernel"},
             "gpu_launches": launches,

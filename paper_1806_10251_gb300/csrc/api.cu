@@ -211,14 +211,16 @@ StepParams make_params(const lbm_ctx *c)
     int Ly = c->Ly_option;
     if (Ly <= 0) {
         // at least four items per resident warp (handed out dynamically) and
-        // segments of at most 16 rows: a warp works through an item's rows one
+        // segments of at most 14 rows: a warp works through an item's rows one
         // after another, so short items keep the latency of a small domain's
         // step and the tail short, while each item re-reads four halo source
-        // rows (4096^2 on GB300: 16 rows 74.0, 24 rows 72.9, 8 rows 67.9 GLUPS)
+        // rows (4096^2 FP32 on GB300, phase-ordered items: 8 rows 76.8, 12 rows
+        // 78.4, 14 rows 78.5, 16 rows 77.7, 24 rows 76.2 GLUPS; FP16 14 and 16
+        // rows 75.3)
         int nseg = (4 * resident + p.nstrips - 1) / p.nstrips;
         if (nseg < 1) nseg = 1;
         Ly = (c->ny + nseg - 1) / nseg;
-        if (Ly > 16) Ly = 16;
+        if (Ly > 14) Ly = 14;
         if (Ly < 1) Ly = 1;
     }
     if (Ly > c->ny) Ly = c->ny;
