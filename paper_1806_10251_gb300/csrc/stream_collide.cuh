@@ -337,9 +337,10 @@ __device__ __forceinline__ bool run_item(WarpCtx &w, const StepParams &p, const 
         };
         // Row r (sources r - 1 .. r + 1 landed) for the lane's cell and the halo
         // columns.  FAST rows have no boundary logic at all; other rows of
-        // domains without solids load like FAST rows and let only the lanes on
-        // a wall cell (and the halo lanes) replace the populations whose
-        // source lies beyond the wall; domains with solids take the general path.
+        // items that meet no solid load like FAST rows and let only the lanes
+        // on a wall cell (and the halo lanes) replace the populations whose
+        // source lies beyond the wall; items that meet a solid take the
+        // general path.
         auto produce = [&](auto fast_tag, int r, R(&g)[9], bool &valid, R &rho, R &rho_l, R &rho_r) {
             constexpr bool FAST = decltype(fast_tag)::value;
             if (FAST || !has_solid) {

@@ -320,9 +320,9 @@ __device__ __forceinline__ bool run_item_x2(WarpCtx &w, const StepParams &p, con
     };
     // Row r (sources r - 1 .. r + 1 landed) for the lane's two cells and the
     // halo columns.  FAST rows have no boundary logic at all; other rows of
-    // domains without solids load like FAST rows and let only the cells on a
-    // wall (and the halo lanes) replace the populations whose source lies
-    // beyond the wall; domains with solids take the general path per cell.
+    // items that meet no solid load like FAST rows and let only the cells on
+    // a wall (and the halo lanes) replace the populations whose source lies
+    // beyond the wall; items that meet a solid take the general path per cell.
     // valid: bit c set when cell xe + c is a lattice site of the domain.
     auto produce = [&](auto fast_tag, int r, F2(&g)[9], int &valid, F2 &rho, R &rho_l, R &rho_r) {
         constexpr bool FAST = decltype(fast_tag)::value;
