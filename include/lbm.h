@@ -155,6 +155,15 @@ lbm_status lbm_step(lbm_ctx *ctx, long n);
 lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, long check_every, long max_steps,
                              double wall_seconds, long *steps_done, double *final_residual);
 
+/* Convergence history of the last lbm_run_to_steady call on this context (the
+ * residual histories the paper plots per gamma, Sec. 6): one entry per check,
+ * the step count after it (as lbm_steps_done) and r.  Copies the first
+ * min(capacity, count) entries into the caller-owned arrays steps / residuals
+ * (either may be NULL, capacity >= 0) and stores the number of entries in
+ * *count (not NULL).  Empty before the first run; each run starts a new one.
+ * Host bookkeeping only: no device call. */
+lbm_status lbm_residual_history(lbm_ctx *ctx, long *steps, double *residuals, long capacity, long *count);
+
 /* One convergence check now: residual against the previous check (or the
  * initial state), then the snapshot is replaced.  sums (may be NULL) receives
  * {sum |du|^2, sum |u|^2, sum rho, sum rho ux, sum rho uy} over fluid cells. */

@@ -126,6 +126,8 @@ struct lbm_ctx {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *d_solid = nullptr;
+    std::vector<long> hist_steps;     // lbm_run_to_steady's checks: step count after each
+    std::vector<double> hist_r;       // and its residual
     float *d_force = nullptr;
     double *d_snap_ux = nullptr, *d_snap_uy = nullptr, *d_partials = nullptr, *d_result = nullptr;
     unsigned long long *d_guard = nullptr;
@@ -708,6 +710,8 @@ lbm_status lbm_run_to_steady(lbm_ctx *c, double tol, long check_every, long max_
     long done = 0;
     double r = INFINITY;
     lbm_status st = LBM_ERR_NOT_CONVERGED;
+    c->hist_steps.clear();
+    c->hist_r.clear();
     // fresh snapshot at the starting state
     lbm_status s = lbm_residual(c, nullptr, nullptr);
     if (s != LBM_OK) return s;
@@ -718,6 +722,8 @@ lbm_status lbm_run_to_steady(lbm_ctx *c, double tol, long check_every, long max_
         done += n;
         s = lbm_residual(c, &r, nullptr);
         if (s != LBM_OK) return s;
+        c->hist_steps.push_back(c->steps);
+        c->hist_r.push_back(r);
         if (!isfinite(r)) {
             st = fail(LBM_ERR_DIVERGED, "non-finite velocity after step " + std::to_string(c->steps));
             break;
@@ -742,6 +748,20 @@ lbm_status lbm_run_to_steady(lbm_ctx *c, double tol, long check_every, long max_
     if (steps_done) *steps_done = done;
     if (final_residual) *final_residual = r;
     return st;
+}
+
+lbm_status lbm_residual_history(lbm_ctx *c, long *steps, double *residuals, long capacity, long *count)
+{
+    if (check_ctx(c)) return LBM_ERR_INVALID;
+    if (!count || capacity < 0) return fail(LBM_ERR_INVALID, "count is null or capacity < 0");
+    const long n = (long)c->hist_r.size();
+    const long m = capacity < n ? capacity : n;
+    for (long i = 0; i < m; ++i) {
+        if (steps) steps[i] = c->hist_steps[(size_t)i];
+        if (residuals) residuals[i] = c->hist_r[(size_t)i];
+    }
+    *count = n;
+    return LBM_OK;
 }
 
 lbm_status lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy)

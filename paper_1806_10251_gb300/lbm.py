@@ -93,6 +93,7 @@ SIGNATURES = {
     "lbm_step": (ctypes.c_int, [_P, _L]),
     "lbm_run_to_steady": (ctypes.c_int, [_P, _D, _L, _L, _D, ctypes.POINTER(_L), _DP]),
     "lbm_residual": (ctypes.c_int, [_P, _DP, _DP]),
+    "lbm_residual_history": (ctypes.c_int, [_P, _P, _P, _L, ctypes.POINTER(_L)]),
     "lbm_fields": (ctypes.c_int, [_P, _P, _P, _P]),
     "lbm_get_populations": (ctypes.c_int, [_P, _P]),
     "lbm_set_populations": (ctypes.c_int, [_P, _P]),
@@ -278,6 +279,16 @@ class Solver:
         if s != OK and raise_on_error:
             raise LbmError(s, last_error())
         return s, steps.value, r.value
+
+    def residual_history(self):
+        """(steps, residuals) of the last run_to_steady, one entry per check."""
+        n = ctypes.c_long()
+        check(lib().lbm_residual_history(self._h, None, None, 0, ctypes.byref(n)))
+        steps = np.zeros(n.value, dtype=np.int64)
+        res = np.zeros(n.value)
+        if n.value:
+            check(lib().lbm_residual_history(self._h, _ptr(steps), _ptr(res), n.value, ctypes.byref(n)))
+        return steps, res
 
     def residual(self):
         r = ctypes.c_double()

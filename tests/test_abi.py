@@ -49,6 +49,8 @@ def test_invalid_arguments_rejected_without_device():
     assert L.lbm_create(16, 16, 0.1, 1.5, 0.1, None, ctypes.byref(h)) == lbm.ERR_INVALID
     assert L.lbm_create(16, 16, 0.1, 0.0, 0.1, None, ctypes.byref(h)) == lbm.ERR_INVALID
     assert L.lbm_step(None, 1) == lbm.ERR_INVALID
+    n = ctypes.c_long(-1)
+    assert L.lbm_residual_history(None, None, None, 0, ctypes.byref(n)) == lbm.ERR_INVALID and n.value == -1
     L.lbm_destroy(None)  # NULL-safe
     b, _ = lbm.make_boundaries([(0, 0, 0), (1, 0, 0), (1, 0, 0), (1, 0, 0)])
     assert L.lbm_create(16, 16, 0.1, 0.5, 0.1, ctypes.byref(b), ctypes.byref(h)) == lbm.ERR_INVALID

@@ -311,6 +311,34 @@ def test_run_to_steady_small_cavity_matches_oracle_steady_state():
     assert l2 <= 1e-6, l2
 
 
+def test_residual_history_of_run_to_steady():
+    """lbm_residual_history: one entry per check of the last run_to_steady (step
+    count after the check, residual), the last one the returned residual; a new
+    run starts a new history; a diverging run ends its history with the
+    non-finite residual."""
+    c = wl.cavity(64, 100.0, 0.1, 0.5)
+    g = lbm.solver_from_case(c)
+    st, steps, r = g.run_to_steady(1e-4, 500, 40000, raise_on_error=False)
+    assert st == lbm.OK
+    hs, hr = g.residual_history()
+    assert len(hs) == steps // 500 and steps % 500 == 0
+    assert np.array_equal(hs, 500 * np.arange(1, len(hs) + 1))
+    assert hr[-1] == r and np.all(hr[:-1] >= 1e-4) and hr[-1] < 1e-4
+    assert hr[-1] < 1e-2 * hr[0]
+    st, steps2, _ = g.run_to_steady(1e-300, 100, 300, raise_on_error=False)
+    assert st == lbm.ERR_NOT_CONVERGED and steps2 == 300
+    hs2, hr2 = g.residual_history()
+    assert np.array_equal(hs2, steps + 100 * np.arange(1, 4)) and len(hr2) == 3
+    f = g.populations()
+    f[0, 5, 5] = np.nan
+    g.set_populations(f)
+    st, _, _ = g.run_to_steady(1e-8, 10, 100, raise_on_error=False)
+    assert st == lbm.ERR_DIVERGED
+    _, hr3 = g.residual_history()
+    assert len(hr3) >= 1 and not np.isfinite(hr3[-1]) and np.all(np.isfinite(hr3[:-1]))
+    g.close()
+
+
 def test_diverged_run_reports_status():
     """A state with a NaN (planted on the host through the API) is reported as
     LBM_ERR_DIVERGED, not as convergence."""
